@@ -1,0 +1,517 @@
+"""Pins of the FP64 oracle to facts fixed by the mathematics, not by the oracle.
+
+Every test here runs on the CPU.  Each one checks the oracle against a closed
+form, an invariant of the discretisation, brute force, or an independent
+restatement of a *definition* (the physical Euler flux, the Taylor polynomial
+of the Runge-Kutta scheme, the exact divergence of a smooth field), chosen so
+that a dropped term, a wrong sign or index, or a transposed operand anywhere in
+the oracle fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1304_7654_gb300 import cases as C
+from oracle.hb_oracle import Oracle, d_matrix, roe_flux, van_albada
+
+G = 1.4
+
+
+# ------------------------------------------------------------------ helpers --
+def euler_flux(W, S, vg=(0.0, 0.0, 0.0)):
+    """Physical ALE Euler flux through area vector S (definition, 5 comps)."""
+    rho, u, v, w, p = W
+    S = np.asarray(list(S) + [0.0] * (3 - len(S)))
+    vel = np.array([u, v, w])
+    q = vel @ S
+    qg = np.asarray(list(vg) + [0.0] * (3 - len(vg))) @ S
+    rE = p / (G - 1) + 0.5 * rho * vel @ vel
+    return np.array([rho * (q - qg), *(rho * vel * (q - qg) + p * S), rE * (q - qg) + p * q])
+
+
+def cons5(W):
+    rho, u, v, w, p = W
+    return np.array([rho, rho * u, rho * v, rho * w, p / (G - 1) + 0.5 * rho * (u * u + v * v + w * w)])
+
+
+def rand_state(rng, dim=2):
+    W = np.array([rng.uniform(0.7, 1.3), rng.uniform(-0.6, 0.6), rng.uniform(-0.6, 0.6),
+                  rng.uniform(-0.6, 0.6) if dim == 3 else 0.0, rng.uniform(0.5, 1.0)])
+    return W
+
+
+def interior_blocks(o, A):
+    return [o.interior(A, b) for b in range(len(o.blocks))]
+
+
+# ------------------------------------------------------------ D matrix (A1) --
+@pytest.mark.parametrize("nh", list(range(0, 16)))
+def test_d_matrix_differentiates_harmonics_exactly(nh):
+    ns = 2 * nh + 1
+    D = d_matrix(ns)
+    th = 2 * np.pi * np.arange(ns) / ns
+    for k in range(0, nh + 1):
+        assert np.allclose(D @ np.cos(k * th), -k * np.sin(k * th), atol=1e-12 * max(1, ns))
+        assert np.allclose(D @ np.sin(k * th), k * np.cos(k * th), atol=1e-12 * max(1, ns))
+    # antisymmetric, zero row sums, spectrum i*k for k = -nh..nh
+    assert np.allclose(D, -D.T, atol=0)
+    assert np.allclose(D.sum(axis=1), 0.0, atol=1e-12 * ns)
+    ev = np.sort(np.linalg.eigvals(D).imag)
+    assert np.allclose(ev, np.arange(-nh, nh + 1), atol=1e-9 * ns)
+
+
+@pytest.mark.parametrize("nh", [1, 3, 8])
+def test_d_matrix_aliases_above_nh(nh):
+    ns = 2 * nh + 1
+    D = d_matrix(ns)
+    th = 2 * np.pi * np.arange(ns) / ns
+    k = nh + 1            # aliases to -(nh): derivative is not recovered
+    assert not np.allclose(D @ np.sin(k * th), k * np.cos(k * th), atol=1e-6)
+
+
+def test_d_matrix_three_snapshots_closed_form():
+    # 3-point trigonometric differentiation: D = (1/sqrt 3) [[0,1,-1],[-1,0,1],[1,-1,0]]
+    r = 1 / math.sqrt(3.0)
+    ref = r * np.array([[0, 1, -1], [-1, 0, 1], [1, -1, 0]], dtype=float)
+    assert np.allclose(d_matrix(3), ref, atol=1e-15)
+
+
+# ---------------------------------------------------------- van Albada (A4) --
+def test_van_albada_properties():
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        a, b = rng.normal(size=2)
+        assert van_albada(a, a) == pytest.approx(a, rel=1e-14)
+        assert abs(van_albada(a, -a)) < 1e-15
+        assert van_albada(a, b) == pytest.approx(van_albada(b, a), rel=1e-14)
+        if a * b > 0:   # same sign: limited slope lies between the two differences
+            v = van_albada(a, b)
+            assert min(a, b) - 1e-14 <= v <= max(a, b) + 1e-14
+    assert van_albada(0.0, 0.0) == 0.0
+
+
+# ------------------------------------------------------------------ Roe (A5) --
+@pytest.mark.parametrize("dim", [2, 3])
+def test_roe_consistency(dim):
+    rng = np.random.default_rng(1)
+    for _ in range(50):
+        W = rand_state(rng, dim)
+        S = rng.normal(size=dim)
+        vg = rng.normal(size=dim) * 0.2
+        F = roe_flux(W, W, S, vg, dim=dim)
+        assert np.allclose(F, euler_flux(W, S, vg), rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_roe_property_and_eigenvector_completeness(dim):
+    rng = np.random.default_rng(2)
+    for _ in range(50):
+        WL, WR = rand_state(rng, dim), rand_state(rng, dim)
+        S = rng.normal(size=dim)
+        n = S / np.linalg.norm(S)
+        vg = rng.normal(size=dim) * 0.2
+        # sum_k lambda_k alpha_k r_k = F_R - F_L (per unit area, relative frame)
+        lam = roe_flux(WL, WR, n, vg, dim=dim, mode=1)
+        dF = euler_flux(WR, n, vg) - euler_flux(WL, n, vg)
+        assert np.allclose(lam, dF, rtol=1e-12, atol=1e-12)
+        # sum_k alpha_k r_k = U_R - U_L
+        ar = roe_flux(WL, WR, n, vg, dim=dim, mode=2)
+        assert np.allclose(ar, cons5(WR) - cons5(WL), rtol=1e-12, atol=1e-12)
+
+
+def test_roe_supersonic_upwinding_and_rotation():
+    rng = np.random.default_rng(3)
+    S = np.array([0.7, -0.4])
+    n = S / np.linalg.norm(S)
+    for _ in range(20):
+        WL = rand_state(rng)
+        WR = rand_state(rng)
+        c = math.sqrt(G * WL[4] / WL[0])
+        WL[1:3] = 2.5 * c * n          # supersonic towards R
+        WR[1:3] = 2.5 * c * n * 1.05
+        F = roe_flux(WL, WR, S)
+        assert np.allclose(F, euler_flux(WL, S), rtol=1e-12, atol=1e-12)
+    # rotating states and face together rotates the momentum flux only
+    for _ in range(20):
+        WL, WR = rand_state(rng), rand_state(rng)
+        S = rng.normal(size=2)
+        phi = rng.uniform(0, 2 * np.pi)
+        R = np.array([[math.cos(phi), -math.sin(phi)], [math.sin(phi), math.cos(phi)]])
+        rot = lambda W: np.array([W[0], *(R @ W[1:3]), 0.0, W[4]])
+        F = roe_flux(WL, WR, S)
+        Fr = roe_flux(rot(WL), rot(WR), R @ S)
+        assert np.allclose(Fr[[0, 4]], F[[0, 4]], rtol=1e-12, atol=1e-13)
+        assert np.allclose(Fr[1:3], R @ F[1:3], rtol=1e-12, atol=1e-13)
+
+
+# ------------------------------------------------------------- geometry (A12) --
+@pytest.mark.parametrize("make", [
+    lambda: C.channel(12, 6),
+    lambda: C.ns_ogrid8(64, 24, n_harm=1),
+    lambda: C.periodic_box2d(10, 8),
+    lambda: C.box3d(8, 6, 4, n_harm=1),
+])
+def test_geometry_closed_cells_and_positive_volumes(make):
+    cs = make()
+    o = Oracle(cs)
+    for b, blk in enumerate(cs.blocks):
+        vol, xc, S = o.geometry(b)
+        _, p, g = o.blocks[b]
+        n = blk.n
+        assert vol.min() > 0
+        # sum of outward face vectors of every cell away from the last ghost layer
+        tot = np.zeros_like(xc)
+        for d in range(cs.dim):
+            ax = 2 - d
+            lo = S[d]
+            hi = np.roll(S[d], -1, axis=ax)
+            tot += hi - lo
+        sl = tuple(slice(g[2 - a], g[2 - a] + n[2 - a]) for a in range(3))
+        assert np.abs(tot[sl]).max() < 1e-12 * max(1.0, np.abs(S).max())
+
+
+def test_volumes_fill_the_domain():
+    cs = C.channel(20, 10)
+    o = Oracle(cs)
+    vol, _, _ = o.geometry(0)
+    assert vol[0, 2:-2, 2:-2].sum() == pytest.approx(2.0, rel=1e-13)
+    cs = C.box3d(8, 6, 4, n_harm=1)
+    o = Oracle(cs)
+    vol, _, _ = o.geometry(0)
+    assert vol[2:-2, 2:-2, 2:-2].sum() == pytest.approx(4.0, rel=1e-12)
+
+
+# --------------------------------------------------- freestream preservation --
+def _freestream(cs):
+    o = Oracle(cs)
+    U = o.init_state(np.zeros(C.interior_count(cs)), 0.0)
+    R, sc = o.residual(U)
+    return o, R, sc
+
+
+def test_freestream_channel_all_cells():
+    cs = C.channel(16, 8)
+    cs.ubc_amp = 0.0
+    o, R, sc = _freestream(cs)
+    assert np.max(np.abs(R) / np.maximum(sc, 1e-300)) < 1e-14
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_freestream_pitching_ogrid_away_from_wall(viscous):
+    cs = C.ns_ogrid8(64, 24, n_harm=2, viscous=viscous)
+    o, R, sc = _freestream(cs)
+    for b, blk in enumerate(cs.blocks):
+        r = o.interior(R, b)
+        s = o.interior(sc, b)
+        j0 = 3 if b < 4 else 0          # inner-ring blocks touch the wall
+        j1 = blk.n[1] - (3 if b >= 4 else 0)
+        assert np.max(np.abs(r[:, :, :, j0:j1]) / s[:, :, :, j0:j1]) < 1e-13
+
+
+def test_freestream_box3d():
+    cs = C.box3d(8, 8, 4, n_harm=1, gust=0.0)
+    o, R, sc = _freestream(cs)
+    r = o.interior(R, 0)[:, :, :, 3:, :]
+    s = o.interior(sc, 0)[:, :, :, 3:, :]
+    assert np.max(np.abs(r) / s) < 1e-13
+
+
+# ---------------------------------------------- HB source, steady special case --
+def test_hb_source_vanishes_for_identical_snapshots():
+    steady = C.channel(12, 6, n_harm=0)
+    steady.ubc_amp = 0.0
+    hb = C.channel(12, 6, n_harm=2)
+    hb.ubc_amp = 0.0
+    os_, oh = Oracle(steady), Oracle(hb)
+    rng = np.random.default_rng(4)
+    Us = os_.init_state(rng.uniform(-1, 1, C.interior_count(steady)), 0.01)
+    Is = os_.unpack(Us).reshape(1, -1)
+    Uh = oh.pack(np.repeat(Is, hb.n_snap, axis=0).reshape(-1))
+    Rs = os_.unpack(os_.residual(Us, with_scale=False)).reshape(1, -1)
+    Rh = oh.unpack(oh.residual(Uh, with_scale=False)).reshape(hb.n_snap, -1)
+    for n in range(hb.n_snap):
+        assert np.allclose(Rh[n], Rs[0], rtol=1e-13, atol=1e-16)
+
+
+# ------------------------------------------------------------- conservation --
+def _periodic_multiblock(ni=16, nj=12, **kw):
+    specs = [C.BlockSpec((0, 0), (10, 7)), C.BlockSpec((10, 0), (16, 7)),
+             C.BlockSpec((0, 7), (5, 12)), C.BlockSpec((5, 7), (16, 12), flip=True)]
+    return C.periodic_box2d(ni, nj, specs=specs, **kw)
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_discrete_conservation_periodic(viscous):
+    cs = _periodic_multiblock(viscous=viscous, n_harm=2)
+    o = Oracle(cs)
+    U = o.init_state(C.noise(cs, 12), 0.05)
+    R, sc = o.residual(U)
+    D = d_matrix(cs.n_snap)
+    tot = np.zeros((cs.n_snap, cs.nv))
+    hb = np.zeros((cs.n_snap, cs.nv))
+    scale = 0.0
+    for b in range(len(cs.blocks)):
+        vol, _, _ = o.geometry(b)
+        _, p, g = o.blocks[b]
+        n = cs.blocks[b].n
+        V = vol[:, g[1]:g[1] + n[1], g[0]:g[0] + n[0]]
+        r = o.interior(R, b)
+        u = o.interior(U, b)
+        tot += r.sum(axis=(2, 3, 4))
+        hb += cs.omega * np.einsum("nm,mvkji,kji->nv", D, u, V)
+        scale = max(scale, o.interior(sc, b).sum())
+    # interior fluxes telescope; the HB term sums to zero over snapshots
+    assert np.abs(tot.sum(axis=0)).max() < 1e-13 * scale
+    assert np.abs(tot - hb).max() < 1e-13 * scale
+
+
+# ---------------------------------------------------- cut transparency (A6) --
+def _global_to_blocks(I, specs, blocks):
+    parts = []
+    for sp, blk in zip(specs, blocks):
+        a = I[..., sp.lo[1]:sp.hi[1], sp.lo[0]:sp.hi[0]]
+        if sp.flip:
+            a = a[..., ::-1, ::-1]
+        parts.append(np.ascontiguousarray(a).reshape(-1))
+    return np.concatenate(parts)
+
+
+@pytest.mark.parametrize("kind", ["ogrid8", "channel_flip", "periodic"])
+def test_multiblock_equals_single_block(kind):
+    if kind == "ogrid8":
+        ni, nj = 64, 24
+        one = C.ogrid(ni, nj, n_harm=1, viscous=True)
+        specs = C.ogrid8_specs(ni, nj)
+        many = C.ns_ogrid8(ni, nj, n_harm=1, viscous=True)
+    elif kind == "channel_flip":
+        ni, nj = 16, 8
+        one = C.channel(ni, nj, viscous=True)
+        specs = [C.BlockSpec((0, 0), (9, 8)), C.BlockSpec((9, 0), (16, 3), flip=True),
+                 C.BlockSpec((9, 3), (16, 8))]
+        many = C.channel(ni, nj, blocks=specs, viscous=True)
+    else:
+        ni, nj = 16, 12
+        one = C.periodic_box2d(ni, nj, viscous=True)
+        many = _periodic_multiblock(viscous=True)
+        specs = [C.BlockSpec((0, 0), (10, 7)), C.BlockSpec((10, 0), (16, 7)),
+                 C.BlockSpec((0, 7), (5, 12)), C.BlockSpec((5, 7), (16, 12), flip=True)]
+    o1, om = Oracle(one), Oracle(many)
+    U1 = o1.init_state(C.noise(one, 3), 0.02)
+    I1 = o1.unpack(U1).reshape(one.n_snap, one.nv, nj, ni)
+    Um = om.pack(_global_to_blocks(I1, specs, many.blocks))
+    R1, S1 = o1.residual(U1)
+    Rm = om.residual(Um, with_scale=False)
+    G1 = _global_to_blocks(o1.unpack(R1).reshape(one.n_snap, one.nv, nj, ni), specs, many.blocks)
+    GS = _global_to_blocks(o1.unpack(S1).reshape(one.n_snap, one.nv, nj, ni), specs, many.blocks)
+    assert np.max(np.abs(om.unpack(Rm) - G1) / GS) < 1e-14
+
+
+# --------------------------------------------------------- rotation invariance --
+def test_rotation_invariance_channel():
+    # the limiter acts on Cartesian velocity components; it is odd and
+    # symmetric, so the discrete residual is covariant under quarter turns
+    phi = 0.5 * math.pi
+    cs = C.channel(12, 6, viscous=True)
+    rc = C.channel(12, 6, viscous=True)
+    R2 = np.array([[math.cos(phi), -math.sin(phi)], [math.sin(phi), math.cos(phi)]])
+    for blk in rc.blocks:
+        blk.nodes = np.ascontiguousarray(blk.nodes @ R2.T)
+    rc.alpha0_deg = math.degrees(phi)
+    o, orr = Oracle(cs), Oracle(rc)
+    U = o.init_state(C.noise(cs, 5), 0.02)
+    Ur = U.copy()
+    v = orr.block_view(Ur, 0)
+    m = o.block_view(U, 0)
+    v[:, 1] = R2[0, 0] * m[:, 1] + R2[0, 1] * m[:, 2]
+    v[:, 2] = R2[1, 0] * m[:, 1] + R2[1, 1] * m[:, 2]
+    R, sc = o.residual(U)
+    Rr = orr.residual(Ur, with_scale=False)
+    a, b = o.block_view(R, 0), orr.block_view(Rr, 0)
+    s = o.block_view(sc, 0)
+    exp = a.copy()
+    exp[:, 1] = R2[0, 0] * a[:, 1] + R2[0, 1] * a[:, 2]
+    exp[:, 2] = R2[1, 0] * a[:, 1] + R2[1, 1] * a[:, 2]
+    ss = np.maximum(s, s[:, 1:3].max(axis=1, keepdims=True) * (np.arange(4) >= 0)[None, :, None, None, None])
+    assert np.max(np.abs(b - exp) / np.maximum(ss, 1e-300)) < 1e-13
+    # local time steps are rotation invariant too
+    assert np.allclose(o.time_step(U), orr.time_step(Ur), rtol=1e-13)
+
+
+# ------------------------------------------------ Runge-Kutta scheme (A9) --
+def test_rk_amplification_is_fourth_order_taylor():
+    # uniform periodic grid: every cell has the same time step, so a state that
+    # is uniform in space stays uniform and only the HB source acts
+    cs = C.periodic_box2d(6, 5, n_harm=2, perturb=0.0)
+    o = Oracle(cs)
+    ns, nv = cs.n_snap, cs.nv
+    rng = np.random.default_rng(6)
+    base = np.array([1.0, 0.3, 0.1, 1 / (G - 1) / G + 0.05])
+    snap = base[None, :] * (1 + 0.05 * rng.uniform(-1, 1, size=(ns, nv)))
+    I = np.broadcast_to(snap[:, :, None, None, None], (ns, nv, 1, 5, 6))
+    U = o.pack(I.reshape(-1))
+    dt = o.interior(o.time_step(U), 0)[:, 0, 0]          # [n][j][i]
+    vol, _, _ = o.geometry(0)
+    U1, _ = o.rk_smooth(U, 1)
+    out = o.interior(U1, 0)
+    D = d_matrix(ns)
+    for (j, i) in [(0, 0), (2, 3), (4, 5)]:
+        Z = -np.diag(dt[:, j, i]) @ (cs.omega * D)        # dU/dtau = -(1/V) R = -omega D U
+        P = np.eye(ns) + Z + Z @ Z / 2 + Z @ Z @ Z / 6 + Z @ Z @ Z @ Z / 24
+        exp = P @ snap
+        assert np.allclose(out[:, :, 0, j, i], exp, rtol=1e-12, atol=1e-13)
+
+
+def test_rk_norms_are_rms_of_first_stage_residual():
+    cs = C.channel(12, 6, n_harm=1)
+    o = Oracle(cs)
+    U = o.init_state(C.noise(cs), 0.01)
+    R = o.residual(U, with_scale=False)
+    vol, _, _ = o.geometry(0)
+    r = o.interior(R, 0) / vol[None, None, 0:1, 2:-2, 2:-2]
+    exp = np.sqrt(np.mean(r ** 2, axis=(0, 2, 3, 4)))
+    _, norms = o.rk_smooth(U, 1)
+    assert np.allclose(norms[0], exp, rtol=1e-13)
+
+
+# --------------------------------------- manufactured-solution order (A18) --
+def _mms_prim(x, y, t):
+    s = 1 + 0.05 * np.sin(t)
+    rho = (1 + 0.1 * x + 0.05 * np.exp(0.5 * y)) * s
+    u = 0.3 + 0.1 * y + 0.05 * np.exp(0.3 * x)
+    v = 0.1 + 0.05 * x + 0.1 * y * y
+    p = 1 / G * (1 + 0.1 * x + 0.05 * y + 0.02 * np.exp(0.2 * y)) * s
+    return rho, u, v, p
+
+
+def _fd(f, x, h=1e-3):
+    return (-f(x + 2 * h) + 8 * f(x + h) - 8 * f(x - h) + f(x - 2 * h)) / (12 * h)
+
+
+def _mms_flux(x, y, t, nx, ny, mu, kap):
+    rho, u, v, p = _mms_prim(x, y, t)
+    q = u * nx + v * ny
+    E = p / (G - 1) / rho + 0.5 * (u * u + v * v)
+    F = np.array([rho * q, rho * u * q + p * nx, rho * v * q + p * ny, (rho * E + p) * q])
+    if mu == 0.0:
+        return F
+    T = lambda xx, yy: G * _mms_prim(xx, yy, t)[3] / _mms_prim(xx, yy, t)[0]
+    ux = _fd(lambda a: _mms_prim(a, y, t)[1], x)
+    uy = _fd(lambda a: _mms_prim(x, a, t)[1], y)
+    vx = _fd(lambda a: _mms_prim(a, y, t)[2], x)
+    vy = _fd(lambda a: _mms_prim(x, a, t)[2], y)
+    Tx, Ty = _fd(lambda a: T(a, y), x), _fd(lambda a: T(x, a), y)
+    div = ux + vy
+    txx, tyy, txy = mu * (2 * ux - 2 / 3 * div), mu * (2 * vy - 2 / 3 * div), mu * (uy + vx)
+    Fv = np.array([0 * x, txx * nx + txy * ny, txy * nx + tyy * ny,
+                   u * (txx * nx + txy * ny) + v * (txy * nx + tyy * ny) + kap * (Tx * nx + Ty * ny)])
+    return F - Fv
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_manufactured_solution_truncation_order(viscous):
+    """R_h/V approaches div F(U) + dU/dt at cell centroids at second order (or
+    better) on a smoothly perturbed grid; the time part (one harmonic <= N_H)
+    is exact, so only the spatial error remains."""
+    mach, re = 0.5, 50.0
+    mu = mach / re if viscous else 0.0
+    kap = mu / ((G - 1) * 0.72)
+    errs = []
+    for n in (16, 32, 64):
+        cs = C.channel(n, n // 2, n_harm=1, viscous=viscous)
+        cs.reynolds = re
+        cs.ubc_amp = 0.0
+        o = Oracle(cs)
+        vol, xc, _ = o.geometry(0)
+        X, Y = xc[0, :, :, 0], xc[0, :, :, 1]
+        U = np.zeros(o.size)
+        bv = o.block_view(U, 0)
+        ts = 2 * np.pi * np.arange(3) / 3
+        for k in range(3):
+            rho, u, v, p = _mms_prim(X, Y, ts[k])
+            bv[k] = np.array([rho, rho * u, rho * v, p / (G - 1) + 0.5 * rho * (u * u + v * v)])[:, None]
+        R = o.residual(U, with_scale=False)
+        e = []
+        for k in range(3):
+            div = (_fd(lambda a: _mms_flux(a, Y, ts[k], 1, 0, mu, kap), X)
+                   + _fd(lambda a: _mms_flux(X, a, ts[k], 0, 1, mu, kap), Y))
+            rho_t = lambda tt: np.array([
+                _mms_prim(X, Y, tt)[0], _mms_prim(X, Y, tt)[0] * _mms_prim(X, Y, tt)[1],
+                _mms_prim(X, Y, tt)[0] * _mms_prim(X, Y, tt)[2],
+                _mms_prim(X, Y, tt)[3] / (G - 1) + 0.5 * _mms_prim(X, Y, tt)[0]
+                * (_mms_prim(X, Y, tt)[1] ** 2 + _mms_prim(X, Y, tt)[2] ** 2)])
+            dudt = _fd(rho_t, ts[k]) * cs.omega
+            err = o.block_view(R, 0)[k, :, 0] / vol[0] - div - dudt
+            e.append(err[:, 4:-4, 4:-4])
+        errs.append(np.sqrt(np.mean(np.array(e) ** 2, axis=(0, 2, 3))))
+    errs = np.array(errs)
+    order = np.log2(errs[:-1] / errs[1:])
+    assert (order >= 1.9).all(), order
+
+
+# ----------------------------------------------------------------- forces --
+def test_uniform_pressure_on_closed_body_gives_no_force():
+    cs = C.ogrid(48, 12, n_harm=1, viscous=False, pitch_deg=3.0)
+    o = Oracle(cs)
+    U = np.zeros(o.size)
+    for b in range(len(cs.blocks)):
+        v = o.interior(U, b)
+        v[:, 0] = 1.3
+        v[:, 1:3] = 0.0
+        v[:, 3] = 2.0 / G / (G - 1)           # p = 2 p_inf, fluid at rest
+    coef, J = o.forces(U)
+    assert np.abs(coef[:, :, :2]).max() < 1e-13
+
+
+def test_symmetric_airfoil_at_zero_incidence_has_zero_lift():
+    cs = C.ogrid(48, 16, n_harm=0, viscous=True, pitch_deg=0.0)
+    o = Oracle(cs)
+    U = o.init_state(np.zeros(C.interior_count(cs)), 0.0)
+    U, _ = o.rk_smooth(U, 30)
+    coef, J = o.forces(U)
+    assert abs(coef[0, 0, 0]) < 1e-10 * abs(coef[0, 0, 1])
+    assert abs(J) < 1e-10 * abs(coef[0, 0, 1])
+
+
+# ---------------------------------------------------------- adjoint columns --
+def test_adjoint_columns_dual_match_central_differences():
+    cs = C.adjoint_ogrid4(64, 16, n_harm=1)
+    o = Oracle(cs)
+    U = o.init_state(C.noise(cs), 0.01)
+    U, _ = o.rk_smooth(U, 3)
+    rng = np.random.default_rng(11)
+    psi = rng.normal(size=o.size)
+    cells = C.sample_cells(cs, 6, 11)
+    cols = np.array([[*c, v, n] for c in cells for v in range(cs.nv) for n in (0, cs.n_snap - 1)])
+    exact = o.adjoint_columns(U, psi, 0.7, cols, mode=0)
+    fd = o.adjoint_columns(U, psi, 0.7, cols, mode=1, h=1e-6)
+    scale = np.abs(exact).max()
+    assert np.max(np.abs(exact - fd)) < 1e-6 * scale
+    # wall-adjacent cells see the functional
+    wall = np.array([[0, 3, 0, 0, v, 0] for v in range(cs.nv)])
+    ej = o.adjoint_columns(U, psi * 0, 1.0, wall, mode=0)
+    fj = o.adjoint_columns(U, psi * 0, 1.0, wall, mode=1, h=1e-6)
+    assert np.abs(ej).max() > 0
+    assert np.max(np.abs(ej - fj)) < 1e-6 * np.abs(ej).max()
+
+
+def test_multiblock_equals_single_block_3d():
+    ni, nj, nk = 8, 6, 6
+    one = C.box3d(ni, nj, nk, n_harm=1)
+    specs = [C.BlockSpec((0, 0, 0), (5, 6, 3)), C.BlockSpec((5, 0, 0), (8, 6, 3)),
+             C.BlockSpec((0, 0, 3), (8, 4, 6)), C.BlockSpec((0, 4, 3), (8, 6, 6))]
+    many = C.box3d(ni, nj, nk, n_harm=1, specs=specs)
+    o1, om = Oracle(one), Oracle(many)
+    U1 = o1.init_state(C.noise(one, 3), 0.02)
+    I1 = o1.unpack(U1).reshape(one.n_snap, one.nv, nk, nj, ni)
+
+    def split(A):
+        return np.concatenate([np.ascontiguousarray(
+            A[..., s.lo[2]:s.hi[2], s.lo[1]:s.hi[1], s.lo[0]:s.hi[0]]).reshape(-1) for s in specs])
+
+    R1, S1 = o1.residual(U1)
+    Rm = om.residual(om.pack(split(I1)), with_scale=False)
+    shp = (one.n_snap, one.nv, nk, nj, ni)
+    ref = split(o1.unpack(R1).reshape(shp))
+    sc = split(o1.unpack(S1).reshape(shp))
+    assert np.max(np.abs(om.unpack(Rm) - ref) / sc) < 1e-14
