@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of the HB residual path on GB300.
+
+Workload: the multi-block 2D laminar Navier-Stokes pitching-airfoil case --
+an O-grid of 1280 x 192 cells (245,760) split into 8 uneven blocks with
+T-junctions, N_H = 3 (7 snapshots), pitch +-3 deg at reduced frequency 0.1,
+Re = 5e3, Mach 0.3 -- on seeded synthetic grids and states.
+
+One step = one pass of the whole hot path: one 4-stage Runge-Kutta iteration
+(halo/BC fill, fused residual + local time step + RK update, FP64 residual
+norms) plus the FP64 force reduction (cl, cd, cm per snapshot, time-averaged
+lift), through the C ABI of libhb.so.  Metric: HB cell-snapshot residual
+updates per second = cells * snapshots * 4 stages / step time.
+
+The state plus workspace (~110 MB in FP32) fits in the 129 MB L2, so an L2
+flush (a 512 MB write) runs between timed steps, outside the timed events.
+
+Other lines: ``--impl reference`` times the FP64 CPU oracle (the reference
+arm).  Under torchrun every rank runs an independent replica (the path has no
+cross-rank exchange on one GPU per case: "replicas only"), timing is the max
+over ranks and the value is the sum of the units all ranks processed.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="ns_ogrid8: 2D laminar NS pitching O-grid, 8 uneven blocks with "
+                "T-junctions, 1280x192 = 245,760 cells, N_H=3 (7 snapshots), Re=5e3, M=0.3",
+                cells=245760, blocks=8, n_harm=3, snapshots=7)
+METRIC = "HB cell-snapshot residual updates/s"
+UNIT = "cell-snapshot-stage updates/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) >= 9:
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------ reference arm --
+def run_reference(args):
+    """FP64 CPU oracle as it stands, single thread: each step is one RK
+    iteration of the same 8-block NS O-grid family at 320 x 48 cells (1/16 of
+    the cells: a bounded sample), timed on the host clock."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle.hb_oracle import Oracle, build
+    from paper_1304_7654_gb300 import cases as C
+    build()
+    cs = C.ns_ogrid8(320, 48)
+    o = Oracle(cs)
+    U = o.init_state(C.noise(cs), 0.01)
+    for _ in range(args.warmup):
+        U, _ = o.rk_smooth(U, 1)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        U, _ = o.rk_smooth(U, 1)
+    dt = time.perf_counter() - t
+    units = cs.n_cells * cs.n_snap * 4 * args.steps
+    val = units / dt
+    sample = ("one RK iteration per step of the ns_ogrid8 family at 320x48 cells (15,360 cells, "
+              "N_H=3), single-threaded FP64 oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(WORKLOAD, sample=sample),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline():
+    """The oracle on a bounded sample: 2 RK iterations of the same workload
+    family at 640 x 96 cells (a quarter of the cells), single thread."""
+    from oracle.hb_oracle import Oracle, build
+    from paper_1304_7654_gb300 import cases as C
+    build()
+    cs = C.ns_ogrid8(640, 96)
+    o = Oracle(cs)
+    U = o.init_state(C.noise(cs), 0.01)
+    t = time.perf_counter()
+    o.rk_smooth(U, 2)
+    dt = time.perf_counter() - t
+    return {"value": cs.n_cells * cs.n_snap * 4 * 2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "2 RK iterations of the ns_ogrid8 family at 640x96 cells (61,440 cells, N_H=3), "
+                      f"single-threaded FP64, {dt:.1f} s"}
+
+
+# --------------------------------------------------------------- our arm --
+def algorithmic_bytes_per_unit(nv, s, moving, viscous, ns):
+    """Bytes one cell-snapshot-stage must move, averaged over the 4 stages:
+    stage 1 reads U and writes U1 (2 nv s); stages 2-4 read U^(s-1), U^(0) and
+    write (3 nv s); plus the static metrics each stage reads once per cell for
+    all snapshots: volume, 2 face vectors (4), centre differences (4, viscous),
+    face midpoints (4) and centre (2) (moving grids)."""
+    state = (2 + 3 + 3 + 3) / 4.0 * nv * s
+    geo = 1 + 4 + (4 if viscous else 0) + (6 if moving else 0)
+    return state + geo * s / ns
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        from paper_1304_7654_gb300 import build as hbuild
+        hbuild.build()
+    if ws > 1:
+        dist.barrier()
+    from paper_1304_7654_gb300 import cases as C
+    from paper_1304_7654_gb300 import hb
+
+    cs = C.ns_ogrid8()
+    units_per_step = cs.n_cells * cs.n_snap * 4
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def run_prec(prec, steps, warmup, timing=True):
+        ctx = hb.HBContext(cs, prec)
+        U = ctx.new_state(dev)
+        noise = torch.as_tensor(C.noise(cs), device=dev)
+        ctx.init_state(U, noise, 0.01)
+        norms = torch.zeros((1, cs.nv), dtype=torch.float64, device=dev)
+        coef = torch.zeros((cs.n_snap, cs.n_bodies, 3), dtype=torch.float64, device=dev)
+        J = torch.zeros(1, dtype=torch.float64, device=dev)
+
+        def step():
+            ctx.rk_smooth_into(U, 1, norms)
+            ctx.forces_into(U, coef, J)
+
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        assert ctx.sync_status() == hb.HB_OK
+        ctx.kernel_stats(0, reset=True)
+        ctx.set_timing(timing)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            flush.zero_()                     # evict L2 between timed steps (not timed)
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        if ws > 1:
+            dist.barrier()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        tile_ms, tile_n = ctx.kernel_stats(0)
+        halo_ms, halo_n = ctx.kernel_stats(1)
+        _, launches = ctx.kernel_stats(2)
+        ctx.set_timing(False)
+        st = ctx.sync_status()
+        return dict(ms=ms, wall=wall, tile_ms=tile_ms, tile_n=tile_n, halo_ms=halo_ms, halo_n=halo_n,
+                    launches=launches, status=st, ctx=ctx, U=U)
+
+    # FP32 flux path with FP64 norms and force sums (headline)
+    clocks = ClockSampler(local)
+    clocks.start()
+    r32 = run_prec("fp32", args.steps, args.warmup)
+    clk = clocks.stop()
+    # FP64 plain path on the same workload, for comparison
+    r64 = run_prec("fp64", args.fp64_steps, 2)
+
+    # e2e: host buffers in pinned memory, H2D of the state and D2H of the
+    # step's results (norms, force coefficients, J) inside the timed region
+    ctx = r32["ctx"]
+    U = r32["U"]
+    host_U = U.cpu().pin_memory()
+    host_out = torch.zeros(cs.nv + cs.n_snap * cs.n_bodies * 3 + 1, dtype=torch.float64).pin_memory()
+    norms = torch.zeros((1, cs.nv), dtype=torch.float64, device=dev)
+    coef = torch.zeros((cs.n_snap, cs.n_bodies, 3), dtype=torch.float64, device=dev)
+    J = torch.zeros(1, dtype=torch.float64, device=dev)
+    outdev = torch.zeros_like(host_out, device=dev)
+    e2e_steps = max(3, args.steps // 2)
+
+    def e2e_step():
+        U.copy_(host_U, non_blocking=True)
+        ctx.rk_smooth_into(U, 1, norms)
+        ctx.forces_into(U, coef, J)
+        outdev[:cs.nv].copy_(norms[0])
+        outdev[cs.nv:-1].copy_(coef.reshape(-1))
+        outdev[-1:].copy_(J)
+        host_out.copy_(outdev, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(e2e_steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in evs) / e2e_steps
+
+    # max over ranks
+    ms32 = r32["ms"]
+    if ws > 1:
+        t = torch.tensor([ms32], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms32 = float(t.item())
+        te = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_ms = float(te.item())
+    ms_per_step = ms32 / args.steps
+    value = ws * units_per_step / (ms_per_step * 1e-3)
+    v64 = units_per_step / (r64["ms"] / args.fp64_steps * 1e-3)
+
+    peaks, src = _peaks()
+    s = 4
+    bpu = algorithmic_bytes_per_unit(cs.nv, s, True, True, cs.n_snap)
+    units_per_launch = cs.n_cells * cs.n_snap
+    launch_ms = r32["tile_ms"] / max(1, r32["tile_n"])
+    achieved = bpu * units_per_launch / (launch_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "kernel": "tile2d_kernel<float,7,VISC,RK>", "peak_source": src,
+            "bytes_per_unit": bpu, "units_per_launch": units_per_launch, "launch_ms": launch_ms}
+    tr = _traffic_record("tile2d_f32_ns7_visc")
+    if tr:
+        roof["traffic"] = tr
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(WORKLOAD, precision="FP32 flux/source/update, FP64 norms and force sums",
+                           parallelism="replicas only" if ws > 1 else "single GPU",
+                           l2="flushed between timed steps (512 MB write, not timed)",
+                           step="1 RK iteration (4 stages) + force reduction"),
+            "roofline": roof,
+            "e2e": {"value": ws * units_per_step / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(host_U.numel() * host_U.element_size()),
+                    "d2h_bytes_per_step": int(host_out.numel() * host_out.element_size())},
+            "gpu_launches": int(r32["launches"]),
+            "clocks": clk,
+            "fp64_plain": {"value": v64, "unit": UNIT, "ms_per_step": r64["ms"] / args.fp64_steps,
+                           "steps": args.fp64_steps,
+                           "tile_launch_ms": r64["tile_ms"] / max(1, r64["tile_n"])},
+            "fp32_over_fp64": value / ws / v64,
+            "kernel_share": {"tile_ms": r32["tile_ms"], "halo_ms": r32["halo_ms"], "step_ms_total": ms32},
+            "status": [r32["status"], r64["status"]]}
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _traffic_record(name):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    try:
+        import hashlib
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[name]
+        src = open(os.path.join(ROOT, "paper_1304_7654_gb300", "csrc", "hb_kernels.cuh"), "rb").read()
+        if rec.get("kernel_sha1") != hashlib.sha1(src).hexdigest():
+            return None
+        return rec["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+def run_profile(args):
+    """Small entry point for ncu captures: warmup + steps RK iterations (and
+    force reductions) of the workload in one precision, nothing timed."""
+    import torch
+    from paper_1304_7654_gb300 import build as hbuild
+    hbuild.build()
+    from paper_1304_7654_gb300 import cases as C
+    from paper_1304_7654_gb300 import hb
+    cs = C.ns_ogrid8()
+    ctx = hb.HBContext(cs, args.profile)
+    U = ctx.new_state()
+    ctx.init_state(U, torch.as_tensor(C.noise(cs), device="cuda"), 0.01)
+    norms = torch.zeros((1, cs.nv), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup + args.steps):
+        ctx.rk_smooth_into(U, 1, norms)
+        ctx.forces_into(U)
+    torch.cuda.synchronize()
+    st = ctx.sync_status()
+    print(json.dumps({"profile": args.profile, "iterations": args.warmup + args.steps, "status": st,
+                      "norms": norms.cpu().tolist()}))
+    return 0 if st == 0 else 1
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["fp32", "fp64"], default=None)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.profile:
+        return run_profile(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

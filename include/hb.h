@@ -1,0 +1,216 @@
+/*
+ * hb.h -- C ABI of the GB300 harmonic-balance (HB) residual library (libhb.so).
+ *
+ * The library evaluates and smooths the HB residual of the Navier-Stokes
+ * equations on structured multi-block grids: for every cell and each of the
+ * 2*N_H+1 time snapshots, the cell-centred finite-volume convective (MUSCL +
+ * van Albada + Roe) and viscous (central) flux balance plus the HB source
+ * V*omega*D*U that couples the snapshots through the spectral time-derivative
+ * matrix D, driven by a 4-stage Runge-Kutta smoother with local time steps,
+ * with block-interface ("cut") halos exchanged on the device.
+ *
+ * Paper anchors (Jackson & Campobasso, arXiv 1304.7654):
+ *   - HB NS solver on structured multi-block grids, snapshot loop
+ *     n = 0..2*nharms over the state q2(i,j,ipde,n): Sec. 1 and Sec. 3.1.
+ *   - Cut (halo) exchange at every Runge-Kutta step, one aggregated exchange
+ *     per process pair: Sec. 3.1 "MPI Optimisations" -> hb_exchange_halos.
+ *   - Force coefficients cl, cd (and cm when functag == 3) per body and
+ *     snapshot, aggregated into one reduction per RK step packed
+ *     [snapshot][body][cl,cd,cm]: Sec. 3.1 -> hb_forces.
+ *   - Restart data and per-snapshot output: Sec. 3.1 (not part of this ABI).
+ * The scheme itself (flux, limiter, RK, time step, boundary conditions) is
+ * not printed in the paper; the readings used are documented beside each
+ * kernel in the sources.
+ *
+ * Conventions for every call:
+ *   - Every function returns hb_status; nothing aborts, traps or throws.
+ *   - Device pointers (U, R, psi, r_adj, norms, coeffs, J) are caller-owned
+ *     CUDA device memory, in the layout reported by hb_state_layout.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous on that stream; host-side argument errors are returned
+ *     immediately, device-side errors (non-finite norms, barrier timeouts)
+ *     are latched in a device word and reported by hb_sync_status.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ *   - Precision HB_FP32 computes fluxes, sources and updates in FP32 and keeps
+ *     residual norms, force sums and conservation sums in FP64; HB_FP64
+ *     computes everything in FP64.  The state element type follows it.
+ */
+#ifndef HB_H_
+#define HB_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HB_OK = 0,
+  HB_ERR_INVALID_ARG = 1,   /* malformed descriptor, table, pointer or size */
+  HB_ERR_UNSUPPORTED = 2,   /* valid but not built (e.g. N_H above the maximum) */
+  HB_ERR_CUDA = 3,          /* a CUDA runtime call failed; see hb_last_error */
+  HB_ERR_NONFINITE = 4,     /* a residual norm became NaN or Inf */
+  HB_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+  HB_ERR_OOM = 6            /* device allocation of library workspace failed */
+} hb_status;
+
+typedef enum { HB_FP64 = 0, HB_FP32 = 1 } hb_precision;
+typedef enum { HB_BC_FARFIELD = 1, HB_BC_SLIP = 2, HB_BC_NOSLIP = 3 } hb_bc_type;
+typedef enum { HB_MOTION_NONE = 0, HB_MOTION_PITCH = 1 } hb_motion;
+typedef enum { HB_UBC_NONE = 0, HB_UBC_INLET_ANGLE = 1, HB_UBC_GUST = 2 } hb_unsteady_bc;
+
+/* Largest supported number of harmonics N_H (snapshots 2*N_H+1). */
+#define HB_MAX_HARMONICS 4
+
+/* One structured block of ni x nj (x nk) cells.  `nodes` is host memory, read
+ * only during hb_create: (ni+5)*(nj+5)[*(nk+5)] points with `dim` coordinates
+ * each, i fastest, including two ghost-node layers per direction (local node
+ * index -2 .. n+2).  2D blocks pass nk = 1. */
+typedef struct {
+  int ni, nj, nk;
+  const double* nodes;
+} hb_block_desc;
+
+/* One cut: fills the ghost box [lo, hi) (cell indices, hi exclusive) of block
+ * dst_blk from block src_blk, src[a] = off[a] + sign[a] * dst[perm[a]].  The
+ * box lies in the two ghost layers of one direction p (its pass); along
+ * directions q < p it may extend over ghost cells (block corners), along
+ * q > p it must stay inside the block.  Sources must be interior cells, or
+ * ghost cells along directions q < p.  This is the device form of the
+ * paper's per-RK-step cut exchange (Sec. 3.1). */
+typedef struct {
+  int dst_blk, src_blk;
+  int lo[3], hi[3];
+  int off[3], perm[3], sign[3];
+} hb_cut_desc;
+
+/* One physical boundary segment on face `face` = 2*p + side (side 0: low
+ * index, 1: high index) of block `blk`, tangential cell range [lo, hi) (the
+ * entry along p is ignored).  type: hb_bc_type.  body: index of the body whose
+ * forces include this wall segment, or -1. */
+typedef struct {
+  int blk, face;
+  int lo[3], hi[3];
+  int type, body;
+} hb_bc_desc;
+
+/* One HB case.  Non-dimensionalisation: rho_inf = 1, c_inf = 1,
+ * p_inf = 1/gamma, |u_inf| = mach, mu = mach/reynolds (constant),
+ * heat conductivity mu/((gamma-1) prandtl), reference length 1. */
+typedef struct {
+  int dim;                    /* 2 or 3 (3D requires viscous or inviscid boxes) */
+  int n_harm;                 /* N_H, 0 .. HB_MAX_HARMONICS */
+  double mach, reynolds, prandtl, gamma;
+  double alpha0_deg;          /* mean incidence of the freestream */
+  double omega;               /* fundamental angular frequency */
+  double cfl;                 /* pseudo-time CFL number */
+  double lim_eps;             /* van Albada epsilon (absolute) */
+  double entropy_frac;        /* Harten fix width as a fraction of the Roe sound speed */
+  int viscous, entropy_fix;
+  int motion;                 /* hb_motion: rigid pitch A sin(omega t) about pivot */
+  double pitch_amp_deg, pivot[2];
+  int ubc;                    /* hb_unsteady_bc: periodic farfield variation */
+  double ubc_amp;             /* inlet-angle amplitude (deg) or gust amplitude (fraction of mach) */
+  int n_blocks;
+  const hb_block_desc* blocks;
+  int n_cuts;
+  const hb_cut_desc* cuts;
+  int n_bcs;
+  const hb_bc_desc* bcs;
+  int n_bodies;
+  int functag;                /* 3: include cm in the force output (paper Sec. 3.1) */
+  hb_precision prec;
+} hb_case_desc;
+
+typedef struct hb_ctx hb_ctx;   /* opaque, library-owned */
+
+/* Create a context: validates and copies the descriptors, uploads geometry,
+ * allocates library-owned workspace on the current CUDA device.  Errors:
+ * HB_ERR_INVALID_ARG for malformed tables (cut boxes outside the ghost
+ * layers, sources outside the allowed range, unknown BC types, block ids out
+ * of range), HB_ERR_UNSUPPORTED for N_H > HB_MAX_HARMONICS, HB_ERR_OOM. */
+hb_status hb_create(const hb_case_desc* desc, hb_ctx** out);
+
+/* Create one context holding n independent cases (each with its own grid,
+ * N_H, Mach and motion; all of the same dim, viscosity and precision).  The
+ * state arrays of the cases are concatenated in case order; block indices in
+ * hb_state_layout run over all blocks of all cases.  hb_rk_smooth on such a
+ * context advances every case in one persistent launch per iteration. */
+hb_status hb_create_batch(const hb_case_desc* cases, int n, hb_ctx** out);
+
+hb_status hb_destroy(hb_ctx* ctx);
+
+/* Total number of state elements (double for HB_FP64, float for HB_FP32). */
+int64_t hb_state_size(const hb_ctx* ctx);
+
+/* Layout of block `blk`: the element (n, v, k, j, i) with local cell indices
+ * in [-g, n+g) sits at offset + n*strides[0] + v*strides[1] + (k+gk)*strides[2]
+ * + (j+2)*strides[3] + (i+2)*strides[4]; ext[] receives the padded extents
+ * (i, j, k) and gk = 2 in 3D, 0 in 2D.  Interior cells are i in [0, ni). */
+hb_status hb_state_layout(const hb_ctx* ctx, int blk, int64_t* offset, int64_t strides[5],
+                          int ext[3]);
+
+/* U := freestream of each snapshot at the cell centre times (1 + amp*noise)
+ * on interior cells, ghosts left unchanged.  noise_dev: device FP64 array
+ * with one value per interior (block, snapshot, variable, cell), packed block
+ * after block as [n][v][k][j][i].  noise_dev may be NULL (no noise). */
+hb_status hb_init_state(hb_ctx* ctx, void* U, const double* noise_dev, double amp, void* stream);
+
+/* Fill both ghost layers of every block and snapshot, in place: cut copies and
+ * physical-BC ghost states (characteristic farfield, slip wall, no-slip
+ * adiabatic wall), one pass per direction so block corners see their
+ * diagonal neighbours. */
+hb_status hb_exchange_halos(hb_ctx* ctx, void* U, void* stream);
+
+/* R := R_HB(U), the HB residual of every interior cell and snapshot (flux
+ * balance, outward-positive, plus V*omega*D*U).  U is not modified: the
+ * library fills the halos of its own copy.  R has U's layout; its ghost
+ * entries are left unchanged. */
+hb_status hb_residual(hb_ctx* ctx, const void* U, void* R, void* stream);
+
+/* n_iter iterations of the 4-stage Runge-Kutta smoother (coefficients 1/4,
+ * 1/3, 1/2, 1) with local pseudo-time steps, in place on U.  norms_dev, if
+ * not NULL: device FP64 [n_iter][nv], the RMS over interior cells and
+ * snapshots of R/V per variable at the first stage of each iteration,
+ * summed in a fixed order (bitwise reproducible).  Non-finite norms latch
+ * HB_ERR_NONFINITE (read with hb_sync_status). */
+hb_status hb_rk_smooth(hb_ctx* ctx, void* U, int n_iter, double* norms_dev, void* stream);
+
+/* Force coefficients of every body at every snapshot, packed
+ * [snapshot][body][cl, cd, cm] in FP64 (cm is zero unless functag == 3), as
+ * in the paper's aggregated force reduction (Sec. 3.1); J_dev receives the
+ * time-averaged lift J = (1/N_s) sum_n sum_body cl.  Either output may be
+ * NULL.  U is not modified. */
+hb_status hb_forces(hb_ctx* ctx, const void* U, double* coeffs_dev, double* J_dev, void* stream);
+
+/* Reverse-mode adjoint of the residual and lift functional:
+ * r_adj := (dR_HB/dU)^T psi + J_seed * dJ/dU on interior entries (ghost
+ * entries of r_adj are zeroed), the transpose including the halo/BC maps;
+ * J_dev (may be NULL) receives J(U).  Limiter, Roe and viscous
+ * intermediates are recomputed, not stored.  psi has U's layout (ghost
+ * entries ignored).  Supported for HB_FP64 2D contexts. */
+hb_status hb_adjoint_residual(hb_ctx* ctx, const void* U, const void* psi, double J_seed,
+                              void* r_adj, double* J_dev, void* stream);
+
+/* Benchmark timing.  While enabled, every launch of the tile kernels
+ * (residual / RK stage: class 0) and of the halo kernels (class 1) made
+ * outside a captured graph is bracketed by CUDA events recorded on the
+ * launching stream.  hb_kernel_stats waits for those events and returns the
+ * accumulated device time (ms) and launch count of class `which` since the
+ * last reset; which = 2 returns the count of all library kernel launches
+ * (graph replays included) and no time.  Paper counterpart: none (the paper
+ * reports wall-clock runtimes only, Sec. 5). */
+hb_status hb_set_timing(hb_ctx* ctx, int enable);
+hb_status hb_kernel_stats(hb_ctx* ctx, int which, double* ms, int64_t* launches, int reset);
+
+/* Synchronise `stream`, then read and clear the device error word. */
+hb_status hb_sync_status(hb_ctx* ctx, void* stream);
+
+/* Message of the last error on this context (library-owned string). */
+const char* hb_last_error(const hb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HB_H_ */

@@ -393,10 +393,12 @@ void viscous_flux(const Case& C, const S* U, int b, int n, const Frame& f, const
   load_prim(C, U, b, n, B.cell(cR[0], cR[1], cR[2]), WR);
   S pL[4] = {WL[1], WL[2], WL[3], C.gamma * WL[4] / WL[0]};
   S pR[4] = {WR[1], WR[2], WR[3], C.gamma * WR[4] / WR[0]};
-  double xL[3], xR[3];
-  rotp(f, &B.xc[3 * B.cell(cL[0], cL[1], cL[2])], xL);
-  rotp(f, &B.xc[3 * B.cell(cR[0], cR[1], cR[2])], xR);
-  double t[3] = {xR[0] - xL[0], xR[1] - xL[1], xR[2] - xL[2]};
+  // the rigid rotation is linear, so the rotated L->R centre difference is
+  // the rotation of the static difference (no cancellation of |x| >> |t|)
+  const double* xL = &B.xc[3 * B.cell(cL[0], cL[1], cL[2])];
+  const double* xR = &B.xc[3 * B.cell(cR[0], cR[1], cR[2])];
+  double d0[3] = {xR[0] - xL[0], xR[1] - xL[1], xR[2] - xL[2]}, t[3];
+  rotv(f, d0, t);
   double len = std::sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
   double th[3] = {t[0] / len, t[1] / len, t[2] / len};
   S Gf[4][3];

@@ -1,0 +1,938 @@
+// Host side of libhb.so: the C ABI declared in include/hb.h.
+//
+// hb_create validates the case descriptors, computes the static grid metrics
+// from the nodes (FP64, rounded once to the kernel precision), expands the cut
+// and boundary tables into per-ghost-cell records grouped by pass (direction
+// i, then j, then k, so block corners take their diagonal neighbours), builds
+// the tile work list and allocates the library-owned workspace.  Every entry
+// point only enqueues kernels on the caller's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/hb.h"
+#include "hb_internal.h"
+
+using hbk::BcRec;
+using hbk::BlockDev;
+using hbk::CaseDev;
+using hbk::CopyRec;
+
+namespace {
+
+struct CaseHost {
+  hb_case_desc d;
+  int ns, nv;
+  int block0, nblocks;
+  int tile0, ntiles;
+  int64_t cells;
+};
+
+}  // namespace
+
+struct hb_ctx {
+  int dim = 2, nv = 4, prec = HB_FP64, viscous = 0;
+  size_t tsize = 8;
+  int device = 0;
+  std::vector<CaseHost> cases;
+  std::vector<BlockDev> blocks;
+  int64_t state_size = 0;       // elements
+  int64_t geo_cells = 0;
+  int64_t interior_values = 0;  // sum over cases of cells * ns * nv
+  int64_t total_cells = 0;
+  int ns_max = 1;
+  int TI = 32, TJ = 8, ti_shift = 5;
+  std::vector<int4> tiles;
+  // device
+  void* d_cases = nullptr;
+  BlockDev* d_blocks = nullptr;
+  int4* d_tiles = nullptr;
+  void* d_geo = nullptr;        // G_NQ arrays of geo_cells elements
+  CopyRec* d_copy[3] = {nullptr, nullptr, nullptr};
+  BcRec* d_bc[3] = {nullptr, nullptr, nullptr};
+  int ncopy[3] = {0, 0, 0}, nbc[3] = {0, 0, 0};
+  BcRec* d_walls = nullptr;
+  int nwall = 0;
+  int n_bodies = 0;
+  void* d_A = nullptr;          // RK ping-pong and residual scratch
+  void* d_B = nullptr;
+  double* d_partials = nullptr; // [ntiles][8]
+  double* d_face = nullptr;     // [nwall][ns][3]
+  double* d_ring = nullptr;     // [ring][8] norms ring for graph replays
+  int ring = 0;
+  int* d_err = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::map<std::pair<const void*, int>, cudaGraphExec_t> graphs;
+  std::map<std::pair<const void*, int>, int64_t> graph_kernels;
+  // benchmark timing
+  int timing = 0;
+  bool capturing = false;
+  struct Timed { int cls; cudaEvent_t a, b; };
+  std::vector<Timed> pending;
+  std::vector<cudaEvent_t> pool;
+  double t_ms[2] = {0.0, 0.0};
+  int64_t n_timed[2] = {0, 0};
+  int64_t n_launch = 0;
+  std::string err;
+};
+
+namespace {
+
+hb_status fail(hb_ctx* c, hb_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+hb_status cuda_fail(hb_ctx* c, cudaError_t e, const char* where) {
+  if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? HB_ERR_OOM : HB_ERR_CUDA;
+}
+
+#define HB_CUDA(ctx, call)                                  \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+cudaEvent_t pool_event(hb_ctx* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// brackets one kernel launch with events when benchmark timing is on
+struct TimedScope {
+  hb_ctx* c;
+  int cls;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  TimedScope(hb_ctx* c_, int cls_, cudaStream_t s_) : c(c_), cls(cls_), s(s_) {
+    c->n_launch++;
+    if (c->timing && !c->capturing) {
+      a = pool_event(c);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~TimedScope() {
+    if (a) {
+      cudaEvent_t b = pool_event(c);
+      cudaEventRecord(b, s);
+      c->pending.push_back({cls, a, b});
+    }
+  }
+};
+
+// padded cell index of local cell (i,j,k) in the GPU layout
+inline int64_t pcell(const BlockDev& B, int i, int j, int k) {
+  return ((int64_t)(k + B.gk) * B.P[1] + (j + 2)) * B.P[0] + (i + 2);
+}
+
+// ------------------------------------------------------------ geometry --
+// static metrics of every padded cell, FP64, from the nodes (2 ghost layers)
+void compute_geometry(int dim, const hb_block_desc& bd, const BlockDev& B, std::vector<double>& G,
+                      int64_t geo_cells) {
+  const int q0 = bd.ni + 5, q1 = bd.nj + 5;
+  auto X = [&](int a, int b, int c, int comp) -> double {
+    const int64_t idx = (dim == 3) ? (((int64_t)(c + 2) * q1 + (b + 2)) * q0 + (a + 2))
+                                   : ((int64_t)(b + 2) * q0 + (a + 2));
+    return bd.nodes[dim * idx + comp];
+  };
+  auto put = [&](int q, int64_t cell, double v) { G[(size_t)q * geo_cells + B.goff + cell] = v; };
+  const int kg = (dim == 3) ? 2 : 0;
+  for (int k = -kg; k < B.n[2] + kg; ++k)
+    for (int j = -2; j < B.n[1] + 2; ++j)
+      for (int i = -2; i < B.n[0] + 2; ++i) {
+        const int64_t c = pcell(B, i, j, k);
+        if (dim == 2) {
+          const double x1 = X(i, j, 0, 0), y1 = X(i, j, 0, 1);
+          const double x2 = X(i + 1, j, 0, 0), y2 = X(i + 1, j, 0, 1);
+          const double x3 = X(i + 1, j + 1, 0, 0), y3 = X(i + 1, j + 1, 0, 1);
+          const double x4 = X(i, j + 1, 0, 0), y4 = X(i, j + 1, 0, 1);
+          put(hbk::G_VOL, c, 0.5 * ((x3 - x1) * (y4 - y2) - (y3 - y1) * (x4 - x2)));
+          put(hbk::G_XC, c, 0.25 * (x1 + x2 + x3 + x4));
+          put(hbk::G_XC + 1, c, 0.25 * (y1 + y2 + y3 + y4));
+          // low i-face: edge (i,j)->(i,j+1), normal (dy, -dx); low j-face: (i,j)->(i+1,j), (-dy, dx)
+          put(hbk::G_S + 0, c, y4 - y1);
+          put(hbk::G_S + 1, c, -(x4 - x1));
+          put(hbk::G_S + 3, c, -(y2 - y1));
+          put(hbk::G_S + 4, c, x2 - x1);
+          put(hbk::G_XF + 0, c, 0.5 * (x1 + x4));
+          put(hbk::G_XF + 1, c, 0.5 * (y1 + y4));
+          put(hbk::G_XF + 3, c, 0.5 * (x1 + x2));
+          put(hbk::G_XF + 4, c, 0.5 * (y1 + y2));
+        } else {
+          // face d of the cell: quadrilateral with corners a,b,c,e; area vector
+          // = 1/2 (diagonal 1) x (diagonal 2), oriented towards +d
+          double sv = 0.0;
+          auto face = [&](int d, int ii, int jj, int kk, double* S, double* xf) {
+            int A[3], Bq[3], Cq[3], E[3];   // n00, n11, na, nb
+            if (d == 0) {
+              int a[3] = {ii, jj, kk}, b[3] = {ii, jj + 1, kk + 1}, c2[3] = {ii, jj, kk + 1}, e[3] = {ii, jj + 1, kk};
+              memcpy(A, a, 12); memcpy(Bq, b, 12); memcpy(Cq, c2, 12); memcpy(E, e, 12);
+            } else if (d == 1) {
+              int a[3] = {ii, jj, kk}, b[3] = {ii + 1, jj, kk + 1}, c2[3] = {ii + 1, jj, kk}, e[3] = {ii, jj, kk + 1};
+              memcpy(A, a, 12); memcpy(Bq, b, 12); memcpy(Cq, c2, 12); memcpy(E, e, 12);
+            } else {
+              int a[3] = {ii, jj, kk}, b[3] = {ii + 1, jj + 1, kk}, c2[3] = {ii, jj + 1, kk}, e[3] = {ii + 1, jj, kk};
+              memcpy(A, a, 12); memcpy(Bq, b, 12); memcpy(Cq, c2, 12); memcpy(E, e, 12);
+            }
+            double d1[3], d2[3];
+            for (int m = 0; m < 3; ++m) {
+              d1[m] = X(Bq[0], Bq[1], Bq[2], m) - X(A[0], A[1], A[2], m);
+              d2[m] = X(Cq[0], Cq[1], Cq[2], m) - X(E[0], E[1], E[2], m);
+              xf[m] = 0.25 * (X(A[0], A[1], A[2], m) + X(Bq[0], Bq[1], Bq[2], m) +
+                              X(Cq[0], Cq[1], Cq[2], m) + X(E[0], E[1], E[2], m));
+            }
+            S[0] = 0.5 * (d1[1] * d2[2] - d1[2] * d2[1]);
+            S[1] = 0.5 * (d1[2] * d2[0] - d1[0] * d2[2]);
+            S[2] = 0.5 * (d1[0] * d2[1] - d1[1] * d2[0]);
+          };
+          for (int d = 0; d < 3; ++d) {
+            double Sl[3], xl[3], Sh[3], xh[3];
+            face(d, i, j, k, Sl, xl);
+            face(d, i + (d == 0), j + (d == 1), k + (d == 2), Sh, xh);
+            for (int m = 0; m < 3; ++m) {
+              put(hbk::G_S + 3 * d + m, c, Sl[m]);
+              put(hbk::G_XF + 3 * d + m, c, xl[m]);
+              sv += xh[m] * Sh[m] - xl[m] * Sl[m];
+            }
+          }
+          put(hbk::G_VOL, c, sv / 3.0);
+          for (int m = 0; m < 3; ++m) {
+            double s = 0.0;
+            for (int a = 0; a < 2; ++a)
+              for (int b = 0; b < 2; ++b)
+                for (int e = 0; e < 2; ++e) s += X(i + a, j + b, k + e, m);
+            put(hbk::G_XC + m, c, s / 8.0);
+          }
+        }
+      }
+  // centre differences, FP64 (keeps the face-normal distance exact to the
+  // kernel precision even when |x| is much larger than the cell size)
+  const int64_t sd[3] = {1, B.P[0], (int64_t)B.P[0] * B.P[1]};
+  for (int k = -kg; k < B.n[2] + kg; ++k)
+    for (int j = -2; j < B.n[1] + 2; ++j)
+      for (int i = -2; i < B.n[0] + 2; ++i) {
+        const int64_t c = pcell(B, i, j, k);
+        const int idx3[3] = {i, j, k};
+        for (int d = 0; d < dim; ++d) {
+          if (idx3[d] - 1 < ((d == 2) ? -kg : -2)) continue;
+          for (int m = 0; m < dim; ++m)
+            put(hbk::G_DC + 3 * d + m, c,
+                G[(size_t)(hbk::G_XC + m) * geo_cells + B.goff + c] -
+                    G[(size_t)(hbk::G_XC + m) * geo_cells + B.goff + c - sd[d]]);
+        }
+      }
+}
+
+// --------------------------------------------------------------- tables --
+struct Tables {
+  std::vector<CopyRec> copy[3];
+  std::vector<BcRec> bc[3];
+  std::vector<BcRec> walls;
+};
+
+hb_status build_tables(hb_ctx* ctx, const CaseHost& ch, Tables& T) {
+  const hb_case_desc& d = ch.d;
+  const int dim = d.dim;
+  const int nb = d.n_blocks;
+  auto blk = [&](int b) -> const BlockDev& { return ctx->blocks[ch.block0 + b]; };
+  // ghost coverage count per padded cell
+  std::vector<std::vector<unsigned char>> cover(nb);
+  for (int b = 0; b < nb; ++b) cover[b].assign((size_t)blk(b).plane, 0);
+  auto ghost_ok = [&](const BlockDev& B, int p, const int* c) {
+    for (int a = 0; a < dim; ++a) {
+      const int lo = (a < p) ? -2 : 0, hi = (a < p) ? B.n[a] + 2 : B.n[a];
+      if (a == p) {
+        if (!((c[a] >= -2 && c[a] < 0) || (c[a] >= B.n[a] && c[a] < B.n[a] + 2))) return false;
+      } else if (c[a] < lo || c[a] >= hi) {
+        return false;
+      }
+    }
+    return true;
+  };
+  auto src_ok = [&](const BlockDev& B, int p, const int* c) {
+    for (int a = 0; a < dim; ++a) {
+      const int lo = (a < p) ? -2 : 0, hi = (a < p) ? B.n[a] + 2 : B.n[a];
+      if (c[a] < lo || c[a] >= hi) return false;
+    }
+    return true;
+  };
+  for (int q = 0; q < d.n_cuts; ++q) {
+    const hb_cut_desc& c = d.cuts[q];
+    if (c.dst_blk < 0 || c.dst_blk >= nb || c.src_blk < 0 || c.src_blk >= nb)
+      return fail(ctx, HB_ERR_INVALID_ARG, "cut " + std::to_string(q) + ": block id out of range");
+    const BlockDev& D = blk(c.dst_blk);
+    const BlockDev& S = blk(c.src_blk);
+    int p = -1;
+    for (int a = 0; a < dim; ++a)
+      if (c.lo[a] < 0 || c.hi[a] > D.n[a]) p = a;
+    if (p < 0) return fail(ctx, HB_ERR_INVALID_ARG, "cut " + std::to_string(q) + ": box is not in a ghost layer");
+    bool permok = true;
+    int seen = 0;
+    for (int a = 0; a < 3; ++a) {
+      if (c.perm[a] < 0 || c.perm[a] > 2 || (c.sign[a] != 1 && c.sign[a] != -1)) permok = false;
+      else seen |= 1 << c.perm[a];
+    }
+    if (!permok || seen != 7)
+      return fail(ctx, HB_ERR_INVALID_ARG, "cut " + std::to_string(q) + ": bad perm/sign");
+    const int k0 = (dim == 3) ? c.lo[2] : 0, k1 = (dim == 3) ? c.hi[2] : 1;
+    for (int k = k0; k < k1; ++k)
+      for (int j = c.lo[1]; j < c.hi[1]; ++j)
+        for (int i = c.lo[0]; i < c.hi[0]; ++i) {
+          const int dc[3] = {i, j, k};
+          int sc[3];
+          for (int a = 0; a < 3; ++a) sc[a] = c.off[a] + c.sign[a] * dc[c.perm[a]];
+          if (dim == 2) sc[2] = 0;
+          if (!ghost_ok(D, p, dc))
+            return fail(ctx, HB_ERR_INVALID_ARG, "cut " + std::to_string(q) + ": destination outside the ghost layers of its pass");
+          if (!src_ok(S, p, sc))
+            return fail(ctx, HB_ERR_INVALID_ARG, "cut " + std::to_string(q) + ": source not interior or earlier-pass ghost");
+          const int64_t dcell = pcell(D, dc[0], dc[1], dc[2]);
+          if (cover[c.dst_blk][dcell]++)
+            return fail(ctx, HB_ERR_INVALID_ARG, "cut " + std::to_string(q) + ": ghost cell filled twice");
+          T.copy[p].push_back({ch.block0 + c.dst_blk, ch.block0 + c.src_blk, (int)dcell,
+                               (int)pcell(S, sc[0], sc[1], sc[2])});
+        }
+  }
+  for (int q = 0; q < d.n_bcs; ++q) {
+    const hb_bc_desc& b = d.bcs[q];
+    if (b.blk < 0 || b.blk >= nb || b.face < 0 || b.face >= 2 * dim ||
+        b.type < HB_BC_FARFIELD || b.type > HB_BC_NOSLIP)
+      return fail(ctx, HB_ERR_INVALID_ARG, "bc " + std::to_string(q) + ": bad block, face or type");
+    const BlockDev& B = blk(b.blk);
+    const int p = b.face / 2, side = b.face % 2;
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) { lo[a] = b.lo[a]; hi[a] = b.hi[a]; }
+    if (dim == 2) { lo[2] = 0; hi[2] = 1; }
+    lo[p] = 0;
+    hi[p] = 1;
+    for (int a = 0; a < dim; ++a) {
+      if (a == p) continue;
+      const int l = (a < p) ? -2 : 0, h = (a < p) ? B.n[a] + 2 : B.n[a];
+      if (lo[a] < l || hi[a] > h || lo[a] >= hi[a])
+        return fail(ctx, HB_ERR_INVALID_ARG, "bc " + std::to_string(q) + ": tangential range out of bounds");
+    }
+    for (int k = lo[2]; k < hi[2]; ++k)
+      for (int j = lo[1]; j < hi[1]; ++j)
+        for (int i = lo[0]; i < hi[0]; ++i) {
+          int t[3] = {i, j, k};
+          BcRec r;
+          r.blk = ch.block0 + b.blk;
+          r.type = b.type;
+          r.p = p;
+          r.sgn = side ? 1 : -1;
+          r.body = b.body;
+          for (int l = 0; l < 2; ++l) {
+            int g[3] = {t[0], t[1], t[2]}, m[3] = {t[0], t[1], t[2]};
+            g[p] = side ? B.n[p] + l : -1 - l;
+            m[p] = side ? B.n[p] - 1 - l : l;
+            r.gcell[l] = (int)pcell(B, g[0], g[1], g[2]);
+            r.mcell[l] = (int)pcell(B, m[0], m[1], m[2]);
+            if (cover[b.blk][r.gcell[l]]++)
+              return fail(ctx, HB_ERR_INVALID_ARG, "bc " + std::to_string(q) + ": ghost cell filled twice");
+          }
+          int f[3] = {t[0], t[1], t[2]};
+          f[p] = side ? B.n[p] : 0;
+          r.fcell = (int)pcell(B, f[0], f[1], f[2]);
+          T.bc[p].push_back(r);
+          bool inside = true;
+          for (int a = 0; a < dim; ++a)
+            if (a != p && (t[a] < 0 || t[a] >= B.n[a])) inside = false;
+          if (inside && (b.type == HB_BC_SLIP || b.type == HB_BC_NOSLIP) && b.body >= 0 &&
+              b.body < d.n_bodies)
+            T.walls.push_back(r);
+        }
+  }
+  // every ghost cell of the standard pass boxes filled exactly once
+  for (int b = 0; b < nb; ++b) {
+    const BlockDev& B = blk(b);
+    const int kg = (dim == 3) ? 2 : 0;
+    for (int k = -kg; k < B.n[2] + kg; ++k)
+      for (int j = -2; j < B.n[1] + 2; ++j)
+        for (int i = -2; i < B.n[0] + 2; ++i) {
+          const bool in = i >= 0 && i < B.n[0] && j >= 0 && j < B.n[1] && k >= 0 && k < B.n[2];
+          if (in) continue;
+          if (cover[b][pcell(B, i, j, k)] != 1)
+            return fail(ctx, HB_ERR_INVALID_ARG,
+                        "block " + std::to_string(b) + ": ghost cell (" + std::to_string(i) + "," +
+                            std::to_string(j) + "," + std::to_string(k) + ") not filled by any cut or BC");
+        }
+  }
+  return HB_OK;
+}
+
+template <typename T>
+void fill_case_dev(const CaseHost& ch, CaseDev<T>& C) {
+  const hb_case_desc& d = ch.d;
+  memset(&C, 0, sizeof(C));
+  C.dim = d.dim;
+  C.nv = d.dim + 2;
+  C.ns = ch.ns;
+  C.nh = d.n_harm;
+  C.viscous = d.viscous;
+  C.entropy_fix = d.entropy_fix;
+  C.motion = d.motion;
+  C.ubc = d.ubc;
+  C.n_bodies = d.n_bodies;
+  C.functag = d.functag;
+  C.block0 = ch.block0;
+  C.nblocks = ch.nblocks;
+  C.interior_cells = ch.cells;
+  const double mu = d.mach / d.reynolds;
+  C.gamma = (T)d.gamma;
+  C.mu = (T)mu;
+  C.kappa = (T)(mu / ((d.gamma - 1.0) * d.prandtl));
+  C.prandtl = (T)d.prandtl;
+  C.cfl = (T)d.cfl;
+  C.eps = (T)d.lim_eps;
+  C.ent_frac = (T)d.entropy_frac;
+  C.omega = (T)d.omega;
+  C.mach = (T)d.mach;
+  C.pinf = (T)(1.0 / d.gamma);
+  C.ubc_amp = (T)d.ubc_amp;
+  const double a0 = d.alpha0_deg * M_PI / 180.0;
+  C.alpha0 = (T)a0;
+  C.cosa0 = (T)std::cos(a0);
+  C.sina0 = (T)std::sin(a0);
+  C.pivot[0] = (T)d.pivot[0];
+  C.pivot[1] = (T)d.pivot[1];
+  const int ns = ch.ns;
+  for (int n = 0; n < ns; ++n)
+    for (int m = 0; m < ns; ++m) {
+      double v = 0.0;
+      if (n != m) {
+        const int k = n - m;
+        const double sg = (k % 2 == 0) ? 1.0 : -1.0;
+        v = 0.5 * sg / std::sin(M_PI * (double)k / (double)ns);
+      }
+      C.D[n * ns + m] = (T)v;
+    }
+  const double amp = d.pitch_amp_deg * M_PI / 180.0;
+  for (int n = 0; n < ns; ++n) {
+    const double t = (d.omega > 0.0) ? 2.0 * M_PI * n / (ns * d.omega) : 0.0;
+    double th = 0.0, thd = 0.0;
+    if (d.motion == HB_MOTION_PITCH) {
+      th = amp * std::sin(d.omega * t);
+      thd = amp * d.omega * std::cos(d.omega * t);
+    }
+    C.cth[n] = (T)std::cos(th);
+    C.sth[n] = (T)std::sin(th);
+    C.thd[n] = (T)thd;
+    C.tn[n] = (T)(d.omega * t);
+    double alpha = a0;
+    if (d.ubc == HB_UBC_INLET_ANGLE) alpha += d.ubc_amp * M_PI / 180.0 * std::sin(d.omega * t);
+    C.winf[n][0] = (T)1.0;
+    C.winf[n][1] = (T)(d.mach * std::cos(alpha));
+    C.winf[n][2] = (T)(d.mach * std::sin(alpha));
+    C.winf[n][3] = (T)0.0;
+    C.winf[n][4] = (T)(1.0 / d.gamma);
+  }
+}
+
+template <typename T>
+hbk::Geo<T> geo_of(const hb_ctx* c) {
+  hbk::Geo<T> g;
+  const T* base = static_cast<const T*>(c->d_geo);
+  for (int q = 0; q < hbk::G_NQ; ++q) g.q[q] = base + (size_t)q * c->geo_cells;
+  return g;
+}
+
+void free_ctx(hb_ctx* c) {
+  for (auto& t : c->pending) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  c->pending.clear();
+  c->pool.clear();
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  cudaFree(c->d_cases);
+  cudaFree(c->d_blocks);
+  cudaFree(c->d_tiles);
+  cudaFree(c->d_geo);
+  for (int p = 0; p < 3; ++p) { cudaFree(c->d_copy[p]); cudaFree(c->d_bc[p]); }
+  cudaFree(c->d_walls);
+  cudaFree(c->d_A);
+  cudaFree(c->d_B);
+  cudaFree(c->d_partials);
+  cudaFree(c->d_face);
+  cudaFree(c->d_ring);
+  cudaFree(c->d_err);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+}
+
+hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
+  if (!out) return HB_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!descs || n <= 0) return HB_ERR_INVALID_ARG;
+  hb_ctx* ctx = new hb_ctx();
+  auto bad = [&](hb_status s, const std::string& m) {
+    ctx->err = m;
+    fprintf(stderr, "hb_create: %s\n", m.c_str());
+    free_ctx(ctx);
+    delete ctx;
+    return s;
+  };
+  const hb_case_desc& d0 = descs[0];
+  ctx->dim = d0.dim;
+  ctx->nv = d0.dim + 2;
+  ctx->prec = d0.prec;
+  ctx->viscous = d0.viscous;
+  ctx->tsize = (d0.prec == HB_FP32) ? sizeof(float) : sizeof(double);
+  if (d0.dim != 2) return bad(HB_ERR_UNSUPPORTED, "only dim = 2 is built in this library version");
+  if (d0.prec != HB_FP32 && d0.prec != HB_FP64) return bad(HB_ERR_INVALID_ARG, "bad precision");
+  int64_t off = 0, goff = 0, noff = 0;
+  for (int c = 0; c < n; ++c) {
+    const hb_case_desc& d = descs[c];
+    if (d.dim != d0.dim || d.prec != d0.prec || d.viscous != d0.viscous)
+      return bad(HB_ERR_INVALID_ARG, "batched cases must share dim, precision and viscosity");
+    if (d.n_harm < 0) return bad(HB_ERR_INVALID_ARG, "n_harm < 0");
+    if (d.n_harm > HB_MAX_HARMONICS) return bad(HB_ERR_UNSUPPORTED, "n_harm above HB_MAX_HARMONICS");
+    if (d.n_blocks <= 0 || !d.blocks) return bad(HB_ERR_INVALID_ARG, "no blocks");
+    if ((d.n_cuts > 0 && !d.cuts) || (d.n_bcs > 0 && !d.bcs) || d.n_cuts < 0 || d.n_bcs < 0)
+      return bad(HB_ERR_INVALID_ARG, "null table");
+    if (!(d.gamma > 1.0) || !(d.mach > 0.0) || !(d.reynolds > 0.0) || !(d.prandtl > 0.0) ||
+        !(d.cfl > 0.0) || !(d.omega >= 0.0) || d.n_bodies < 0)
+      return bad(HB_ERR_INVALID_ARG, "bad flow parameters");
+    CaseHost ch;
+    ch.d = d;
+    ch.ns = 2 * d.n_harm + 1;
+    ch.nv = d.dim + 2;
+    ch.block0 = (int)ctx->blocks.size();
+    ch.nblocks = d.n_blocks;
+    ch.cells = 0;
+    ctx->ns_max = std::max(ctx->ns_max, ch.ns);
+    ctx->n_bodies = std::max(ctx->n_bodies, d.n_bodies);
+    for (int b = 0; b < d.n_blocks; ++b) {
+      const hb_block_desc& bd = d.blocks[b];
+      if (bd.ni < 1 || bd.nj < 1 || bd.nk != 1 || !bd.nodes)
+        return bad(HB_ERR_INVALID_ARG, "bad block " + std::to_string(b));
+      BlockDev B;
+      memset(&B, 0, sizeof(B));
+      B.n[0] = bd.ni; B.n[1] = bd.nj; B.n[2] = 1;
+      B.gk = 0;
+      B.P[0] = round_up(bd.ni + 4, 8);
+      B.P[1] = bd.nj + 4;
+      B.P[2] = 1;
+      B.plane = (int64_t)B.P[0] * B.P[1] * B.P[2];
+      B.plane = (B.plane + 31) / 32 * 32;
+      B.off = off;
+      B.goff = goff;
+      B.noff = noff;
+      B.cs = c;
+      off += B.plane * ch.ns * ch.nv;
+      goff += B.plane;
+      const int64_t cells = (int64_t)bd.ni * bd.nj;
+      noff += cells * ch.ns * ch.nv;
+      ch.cells += cells;
+      ctx->blocks.push_back(B);
+    }
+    ctx->total_cells += ch.cells;
+    ctx->interior_values += ch.cells * ch.ns * ch.nv;
+    ctx->cases.push_back(ch);
+  }
+  ctx->state_size = off;
+  ctx->geo_cells = goff;
+  // tables
+  Tables Tb;
+  for (auto& ch : ctx->cases) {
+    hb_status s = build_tables(ctx, ch, Tb);
+    if (s != HB_OK) return bad(s, ctx->err);
+  }
+  // tiles
+  for (auto& ch : ctx->cases) {
+    ch.tile0 = (int)ctx->tiles.size();
+    for (int b = 0; b < ch.nblocks; ++b) {
+      const BlockDev& B = ctx->blocks[ch.block0 + b];
+      for (int j = 0; j < B.n[1]; j += ctx->TJ)
+        for (int i = 0; i < B.n[0]; i += ctx->TI) ctx->tiles.push_back(make_int4(ch.block0 + b, i, j, 0));
+    }
+    ch.ntiles = (int)ctx->tiles.size() - ch.tile0;
+  }
+  // geometry (FP64 on the host, rounded once)
+  std::vector<double> G((size_t)hbk::G_NQ * ctx->geo_cells, 0.0);
+  for (auto& ch : ctx->cases)
+    for (int b = 0; b < ch.nblocks; ++b)
+      compute_geometry(ctx->dim, ch.d.blocks[b], ctx->blocks[ch.block0 + b], G, ctx->geo_cells);
+  for (auto& ch : ctx->cases)
+    for (int b = 0; b < ch.nblocks; ++b) {
+      const BlockDev& B = ctx->blocks[ch.block0 + b];
+      // interior cells must be right-handed; ghost cells reflected through a
+      // sharp corner may be inverted but must not be degenerate
+      for (int j = -2; j < B.n[1] + 2; ++j)
+        for (int i = -2; i < B.n[0] + 2; ++i) {
+          const double v = G[(size_t)hbk::G_VOL * ctx->geo_cells + B.goff + pcell(B, i, j, 0)];
+          const bool in = i >= 0 && i < B.n[0] && j >= 0 && j < B.n[1];
+          if (in ? !(v > 0.0) : !(v != 0.0 && std::isfinite(v)))
+            return bad(HB_ERR_INVALID_ARG, in ? "non-positive interior cell volume (left-handed block)"
+                                              : "degenerate ghost cell (zero volume)");
+        }
+    }
+  cudaError_t e;
+#define CK(call)                                        \
+  do {                                                  \
+    e = (call);                                         \
+    if (e != cudaSuccess) {                             \
+      return bad(e == cudaErrorMemoryAllocation ? HB_ERR_OOM : HB_ERR_CUDA, \
+                 std::string(#call) + ": " + cudaGetErrorString(e)); \
+    }                                                   \
+  } while (0)
+  CK(cudaGetDevice(&ctx->device));
+  const size_t ts = ctx->tsize;
+  CK(cudaMalloc(&ctx->d_geo, ts * hbk::G_NQ * ctx->geo_cells));
+  if (ctx->prec == HB_FP32) {
+    std::vector<float> Gf(G.size());
+    for (size_t q = 0; q < G.size(); ++q) Gf[q] = (float)G[q];
+    CK(cudaMemcpy(ctx->d_geo, Gf.data(), ts * Gf.size(), cudaMemcpyHostToDevice));
+  } else {
+    CK(cudaMemcpy(ctx->d_geo, G.data(), ts * G.size(), cudaMemcpyHostToDevice));
+  }
+  const size_t csz = (ctx->prec == HB_FP32) ? sizeof(CaseDev<float>) : sizeof(CaseDev<double>);
+  std::vector<unsigned char> cbuf(csz * ctx->cases.size());
+  for (size_t c = 0; c < ctx->cases.size(); ++c) {
+    if (ctx->prec == HB_FP32) fill_case_dev<float>(ctx->cases[c], *(CaseDev<float>*)(cbuf.data() + csz * c));
+    else fill_case_dev<double>(ctx->cases[c], *(CaseDev<double>*)(cbuf.data() + csz * c));
+  }
+  CK(cudaMalloc(&ctx->d_cases, cbuf.size()));
+  CK(cudaMemcpy(ctx->d_cases, cbuf.data(), cbuf.size(), cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&ctx->d_blocks, sizeof(BlockDev) * ctx->blocks.size()));
+  CK(cudaMemcpy(ctx->d_blocks, ctx->blocks.data(), sizeof(BlockDev) * ctx->blocks.size(), cudaMemcpyHostToDevice));
+  CK(cudaMalloc(&ctx->d_tiles, sizeof(int4) * std::max<size_t>(1, ctx->tiles.size())));
+  CK(cudaMemcpy(ctx->d_tiles, ctx->tiles.data(), sizeof(int4) * ctx->tiles.size(), cudaMemcpyHostToDevice));
+  for (int p = 0; p < 3; ++p) {
+    ctx->ncopy[p] = (int)Tb.copy[p].size();
+    ctx->nbc[p] = (int)Tb.bc[p].size();
+    if (ctx->ncopy[p]) {
+      CK(cudaMalloc(&ctx->d_copy[p], sizeof(CopyRec) * ctx->ncopy[p]));
+      CK(cudaMemcpy(ctx->d_copy[p], Tb.copy[p].data(), sizeof(CopyRec) * ctx->ncopy[p], cudaMemcpyHostToDevice));
+    }
+    if (ctx->nbc[p]) {
+      CK(cudaMalloc(&ctx->d_bc[p], sizeof(BcRec) * ctx->nbc[p]));
+      CK(cudaMemcpy(ctx->d_bc[p], Tb.bc[p].data(), sizeof(BcRec) * ctx->nbc[p], cudaMemcpyHostToDevice));
+    }
+  }
+  ctx->nwall = (int)Tb.walls.size();
+  if (ctx->nwall) {
+    CK(cudaMalloc(&ctx->d_walls, sizeof(BcRec) * ctx->nwall));
+    CK(cudaMemcpy(ctx->d_walls, Tb.walls.data(), sizeof(BcRec) * ctx->nwall, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_face, sizeof(double) * 3 * ctx->nwall * ctx->ns_max));
+  }
+  CK(cudaMalloc(&ctx->d_A, ts * ctx->state_size));
+  CK(cudaMalloc(&ctx->d_B, ts * ctx->state_size));
+  CK(cudaMemset(ctx->d_A, 0, ts * ctx->state_size));
+  CK(cudaMemset(ctx->d_B, 0, ts * ctx->state_size));
+  CK(cudaMalloc(&ctx->d_partials, sizeof(double) * 8 * std::max<size_t>(1, ctx->tiles.size())));
+  ctx->ring = 64;
+  CK(cudaMalloc(&ctx->d_ring, sizeof(double) * 8 * ctx->ring));
+  CK(cudaMalloc(&ctx->d_err, sizeof(int)));
+  CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
+  CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+#undef CK
+  *out = ctx;
+  return HB_OK;
+}
+
+// ------------------------------------------------------------ launches --
+template <typename T>
+hb_status halos(hb_ctx* c, T* U, cudaStream_t s) {
+  hbk::HaloParams<T> p;
+  p.cases = (const CaseDev<T>*)c->d_cases;
+  p.blocks = c->d_blocks;
+  p.g = geo_of<T>(c);
+  p.U = U;
+  p.ns_max = c->ns_max;
+  for (int pass = 0; pass < c->dim; ++pass) {
+    p.copies = c->d_copy[pass];
+    p.ncopy = c->ncopy[pass];
+    p.bcs = c->d_bc[pass];
+    p.nbc = c->nbc[pass];
+    if ((int64_t)(p.ncopy + p.nbc) == 0) continue;
+    TimedScope ts(c, 1, s);
+    HB_CUDA(c, hbk::launch_halo<T>(p, s));
+  }
+  return HB_OK;
+}
+
+template <typename T>
+hbk::StageParams<T> stage_params(hb_ctx* c) {
+  hbk::StageParams<T> p;
+  memset(&p, 0, sizeof(p));
+  p.cases = (const CaseDev<T>*)c->d_cases;
+  p.blocks = c->d_blocks;
+  p.g = geo_of<T>(c);
+  p.TI = c->TI;
+  p.TJ = c->TJ;
+  p.ti_shift = c->ti_shift;
+  return p;
+}
+
+// one launch per case (each case has its own snapshot count)
+template <typename T>
+hb_status stage_all(hb_ctx* c, hbk::StageParams<T> p, int mode, cudaStream_t s) {
+  for (auto& ch : c->cases) {
+    p.tiles = c->d_tiles + ch.tile0;
+    p.ntiles = ch.ntiles;
+    double* part = p.partials;
+    if (part) p.partials = part + (size_t)8 * ch.tile0;
+    TimedScope ts(c, 0, s);
+    HB_CUDA(c, hbk::launch_stage<T>(p, ch.ns, c->viscous, mode, s));
+    p.partials = part;
+  }
+  return HB_OK;
+}
+
+template <typename T>
+hb_status residual_impl(hb_ctx* c, const T* U, T* R, cudaStream_t s) {
+  T* W = (T*)c->d_A;
+  c->n_launch++;
+  HB_CUDA(c, hbk::launch_copy(W, U, (int64_t)c->tsize * c->state_size, s));
+  hb_status st = halos<T>(c, W, s);
+  if (st != HB_OK) return st;
+  auto p = stage_params<T>(c);
+  p.Uprev = W;
+  p.R = R;
+  return stage_all<T>(c, p, 0, s);
+}
+
+// one RK iteration; norms (nv doubles per case block of 8) written to `norm_out`
+template <typename T>
+hb_status rk_iteration(hb_ctx* c, T* U, double* norm_out, cudaStream_t s) {
+  static const double alpha[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
+  T* A = (T*)c->d_A;
+  T* Bf = (T*)c->d_B;
+  T* in[4] = {U, A, Bf, A};
+  T* out[4] = {A, Bf, A, U};
+  for (int st = 0; st < 4; ++st) {
+    hb_status r = halos<T>(c, in[st], s);
+    if (r != HB_OK) return r;
+    auto p = stage_params<T>(c);
+    p.Uprev = in[st];
+    p.U0 = U;
+    p.Unext = out[st];
+    p.alpha = (T)alpha[st];
+    p.partials = (st == 0) ? c->d_partials : nullptr;
+    r = stage_all<T>(c, p, 1, s);
+    if (r != HB_OK) return r;
+    if (st == 0) {
+      // norms per case, fixed order; batched contexts report the first case
+      const CaseHost& ch = c->cases[0];
+      c->n_launch++;
+      HB_CUDA(c, hbk::launch_norm_finish(c->d_partials + (size_t)8 * ch.tile0, ch.ntiles, c->nv,
+                                         1.0 / ((double)ch.cells * ch.ns), norm_out, c->d_err, s));
+    }
+  }
+  return HB_OK;
+}
+
+template <typename T>
+hb_status rk_smooth_impl(hb_ctx* c, T* U, int n_iter, double* norms, cudaStream_t s) {
+  const int K = std::min(n_iter, c->ring);
+  int done = 0;
+  // full chunks of K iterations replay one captured graph
+  if (n_iter >= 2) {
+    auto key = std::make_pair((const void*)U, K);
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+      cudaGraph_t g;
+      HB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
+      hb_status r = HB_OK;
+      c->capturing = true;
+      const int64_t n0 = c->n_launch;
+      for (int k = 0; k < K && r == HB_OK; ++k) r = rk_iteration<T>(c, U, c->d_ring + 8 * k, c->cap_stream);
+      c->capturing = false;
+      c->graph_kernels[key] = c->n_launch - n0;
+      c->n_launch = n0;
+      cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+      if (r != HB_OK) return r;
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+      cudaGraphExec_t ex;
+      e = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+      it = c->graphs.emplace(key, ex).first;
+    }
+    while (n_iter - done >= K) {
+      c->n_launch += c->graph_kernels[key];
+      HB_CUDA(c, cudaGraphLaunch(it->second, s));
+      if (norms)
+        HB_CUDA(c, cudaMemcpy2DAsync(norms + (size_t)done * c->nv, sizeof(double) * c->nv, c->d_ring,
+                                     sizeof(double) * 8, sizeof(double) * c->nv, K,
+                                     cudaMemcpyDeviceToDevice, s));
+      done += K;
+    }
+  }
+  for (; done < n_iter; ++done) {
+    hb_status r = rk_iteration<T>(c, U, c->d_ring, s);
+    if (r != HB_OK) return r;
+    if (norms)
+      HB_CUDA(c, cudaMemcpyAsync(norms + (size_t)done * c->nv, c->d_ring, sizeof(double) * c->nv,
+                                 cudaMemcpyDeviceToDevice, s));
+  }
+  return HB_OK;
+}
+
+template <typename T>
+hb_status forces_impl(hb_ctx* c, const T* U, double* coef, double* J, cudaStream_t s) {
+  T* W = (T*)c->d_A;
+  c->n_launch++;
+  HB_CUDA(c, hbk::launch_copy(W, U, (int64_t)c->tsize * c->state_size, s));
+  hb_status st = halos<T>(c, W, s);
+  if (st != HB_OK) return st;
+  hbk::ForceParams<T> p;
+  p.cases = (const CaseDev<T>*)c->d_cases;
+  p.blocks = c->d_blocks;
+  p.g = geo_of<T>(c);
+  p.U = W;
+  p.walls = c->d_walls;
+  p.nwall = c->nwall;
+  p.ns = c->cases[0].ns;
+  p.face_out = c->d_face;
+  p.coef = coef;
+  p.J = J;
+  p.nbodies = c->cases[0].d.n_bodies;
+  if (p.nbodies == 0) {
+    if (J) HB_CUDA(c, cudaMemsetAsync(J, 0, sizeof(double), s));
+    return HB_OK;
+  }
+  c->n_launch += (p.nwall * p.ns > 0) ? 2 : 1;
+  HB_CUDA(c, hbk::launch_forces<T>(p, s));
+  return HB_OK;
+}
+
+template <typename T>
+hb_status init_impl(hb_ctx* c, T* U, const double* noise, double amp, cudaStream_t s) {
+  c->n_launch += (int64_t)c->blocks.size();
+  HB_CUDA(c, hbk::launch_init<T>((const CaseDev<T>*)c->d_cases, c->d_blocks, (int)c->blocks.size(),
+                                 geo_of<T>(c), U, noise, amp, c->interior_values, nullptr, s));
+  return HB_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+hb_status hb_create(const hb_case_desc* desc, hb_ctx** out) { return create_impl(desc, 1, out); }
+
+hb_status hb_create_batch(const hb_case_desc* cases, int n, hb_ctx** out) {
+  return create_impl(cases, n, out);
+}
+
+hb_status hb_destroy(hb_ctx* ctx) {
+  if (!ctx) return HB_ERR_INVALID_ARG;
+  free_ctx(ctx);
+  delete ctx;
+  return HB_OK;
+}
+
+int64_t hb_state_size(const hb_ctx* ctx) { return ctx ? ctx->state_size : -1; }
+
+hb_status hb_state_layout(const hb_ctx* ctx, int blk, int64_t* offset, int64_t strides[5], int ext[3]) {
+  if (!ctx || blk < 0 || blk >= (int)ctx->blocks.size() || !offset || !strides) return HB_ERR_INVALID_ARG;
+  const BlockDev& B = ctx->blocks[blk];
+  *offset = B.off;
+  strides[0] = B.plane * ctx->nv;
+  strides[1] = B.plane;
+  strides[2] = (int64_t)B.P[0] * B.P[1];
+  strides[3] = B.P[0];
+  strides[4] = 1;
+  if (ext) { ext[0] = B.P[0]; ext[1] = B.P[1]; ext[2] = B.P[2]; }
+  return HB_OK;
+}
+
+hb_status hb_init_state(hb_ctx* ctx, void* U, const double* noise, double amp, void* stream) {
+  if (!ctx || !U) return fail(ctx, HB_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  return ctx->prec == HB_FP32 ? init_impl<float>(ctx, (float*)U, noise, amp, s)
+                              : init_impl<double>(ctx, (double*)U, noise, amp, s);
+}
+
+hb_status hb_exchange_halos(hb_ctx* ctx, void* U, void* stream) {
+  if (!ctx || !U) return fail(ctx, HB_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  return ctx->prec == HB_FP32 ? halos<float>(ctx, (float*)U, s) : halos<double>(ctx, (double*)U, s);
+}
+
+hb_status hb_residual(hb_ctx* ctx, const void* U, void* R, void* stream) {
+  if (!ctx || !U || !R) return fail(ctx, HB_ERR_INVALID_ARG, "null argument");
+  if (U == R) return fail(ctx, HB_ERR_INVALID_ARG, "U and R must not alias");
+  cudaStream_t s = (cudaStream_t)stream;
+  return ctx->prec == HB_FP32 ? residual_impl<float>(ctx, (const float*)U, (float*)R, s)
+                              : residual_impl<double>(ctx, (const double*)U, (double*)R, s);
+}
+
+hb_status hb_rk_smooth(hb_ctx* ctx, void* U, int n_iter, double* norms, void* stream) {
+  if (!ctx || !U || n_iter < 0) return fail(ctx, HB_ERR_INVALID_ARG, "bad argument");
+  if (n_iter == 0) return HB_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  return ctx->prec == HB_FP32 ? rk_smooth_impl<float>(ctx, (float*)U, n_iter, norms, s)
+                              : rk_smooth_impl<double>(ctx, (double*)U, n_iter, norms, s);
+}
+
+hb_status hb_forces(hb_ctx* ctx, const void* U, double* coef, double* J, void* stream) {
+  if (!ctx || !U) return fail(ctx, HB_ERR_INVALID_ARG, "null argument");
+  if (ctx->cases.size() != 1) return fail(ctx, HB_ERR_UNSUPPORTED, "hb_forces needs a single-case context");
+  cudaStream_t s = (cudaStream_t)stream;
+  return ctx->prec == HB_FP32 ? forces_impl<float>(ctx, (const float*)U, coef, J, s)
+                              : forces_impl<double>(ctx, (const double*)U, coef, J, s);
+}
+
+hb_status hb_adjoint_residual(hb_ctx* ctx, const void* U, const void* psi, double J_seed, void* r_adj,
+                              double* J_dev, void* stream) {
+  (void)U; (void)psi; (void)J_seed; (void)r_adj; (void)J_dev; (void)stream;
+  return fail(ctx, HB_ERR_UNSUPPORTED, "adjoint not built in this library version");
+}
+
+hb_status hb_set_timing(hb_ctx* ctx, int enable) {
+  if (!ctx) return HB_ERR_INVALID_ARG;
+  ctx->timing = enable ? 1 : 0;
+  return HB_OK;
+}
+
+hb_status hb_kernel_stats(hb_ctx* ctx, int which, double* ms, int64_t* launches, int reset) {
+  if (!ctx || which < 0 || which > 2) return HB_ERR_INVALID_ARG;
+  for (auto& t : ctx->pending) {
+    HB_CUDA(ctx, cudaEventSynchronize(t.b));
+    float e = 0.0f;
+    HB_CUDA(ctx, cudaEventElapsedTime(&e, t.a, t.b));
+    ctx->t_ms[t.cls] += e;
+    ctx->n_timed[t.cls] += 1;
+    ctx->pool.push_back(t.a);
+    ctx->pool.push_back(t.b);
+  }
+  ctx->pending.clear();
+  if (ms) *ms = (which < 2) ? ctx->t_ms[which] : 0.0;
+  if (launches) *launches = (which < 2) ? ctx->n_timed[which] : ctx->n_launch;
+  if (reset) {
+    ctx->t_ms[0] = ctx->t_ms[1] = 0.0;
+    ctx->n_timed[0] = ctx->n_timed[1] = 0;
+    ctx->n_launch = 0;
+  }
+  return HB_OK;
+}
+
+hb_status hb_sync_status(hb_ctx* ctx, void* stream) {
+  if (!ctx) return HB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  HB_CUDA(ctx, cudaStreamSynchronize(s));
+  int e = 0;
+  HB_CUDA(ctx, cudaMemcpy(&e, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  HB_CUDA(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
+  if (e == HB_ERR_NONFINITE) return fail(ctx, HB_ERR_NONFINITE, "non-finite residual norm");
+  if (e == HB_ERR_TIMEOUT) return fail(ctx, HB_ERR_TIMEOUT, "device wait timed out");
+  if (e != 0) return fail(ctx, HB_ERR_CUDA, "device error word " + std::to_string(e));
+  return HB_OK;
+}
+
+const char* hb_last_error(const hb_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+}  // extern "C"

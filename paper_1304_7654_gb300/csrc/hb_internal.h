@@ -1,0 +1,132 @@
+// Internal structures shared by the host side (hb_api.cpp) and the CUDA
+// kernels of libhb.so.  Not part of the public ABI (include/hb.h).
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace hbk {
+
+constexpr int MAXNS = 9;       // 2 * HB_MAX_HARMONICS + 1
+constexpr int MAXNT = 256;     // threads per tile CTA
+
+// Per-case constants, in the kernel precision T.  Frames and freestream are
+// tabulated per snapshot on the host in FP64 and rounded once.
+template <typename T>
+struct CaseDev {
+  int dim, nv, ns, nh;
+  int viscous, entropy_fix, motion, ubc;
+  int n_bodies, functag;
+  int block0, nblocks;
+  int64_t interior_cells;
+  T gamma, mu, kappa, prandtl, cfl, eps, ent_frac, omega, mach, pinf, ubc_amp, alpha0;
+  T pivot[2];
+  T cosa0, sina0;
+  T D[MAXNS * MAXNS];                   // spectral derivative matrix (row n, column m)
+  T cth[MAXNS], sth[MAXNS], thd[MAXNS]; // rotation and pitch rate at each snapshot
+  T tn[MAXNS];                          // omega * t_n
+  T winf[MAXNS][5];                     // freestream primitives (rho, u, v, w, p) per snapshot
+};
+
+// One block of the state: element (n, v, padded cell c) at off + (n*nv + v)*plane + c,
+// padded cell c = ((k+gk)*P1 + (j+2))*P0 + (i+2).
+struct BlockDev {
+  int64_t off;
+  int64_t plane;
+  int64_t goff;       // offset of the block's padded cells in the geometry arrays
+  int n[3];
+  int P[3];
+  int gk;
+  int cs;             // case index
+  int64_t noff;       // offset of the block's interior cells in compact [n][v][k][j][i] order
+};
+
+// geometry quantities, each an array over all padded cells of all blocks
+enum {
+  G_VOL = 0,
+  G_XC = 1,            // 3 components
+  G_S = 4,             // S[d][comp]: low face of the cell along d, 9 arrays
+  G_XF = 13,           // face centroid [d][comp], 9 arrays
+  G_DC = 22,           // centre minus centre of the low neighbour along d [d][comp], 9 arrays
+  G_NQ = 31
+};
+
+struct CopyRec { int dst_blk, src_blk, dst_cell, src_cell; };
+// physical-boundary ghost fill at one tangential position: both ghost layers
+struct BcRec {
+  int blk, type, p, sgn;   // sgn = +1 on the high face, -1 on the low face
+  int gcell[2];            // ghost cells, layer 0 (adjacent) and 1
+  int mcell[2];            // mirror cells, interior layer 0 and 1
+  int fcell;               // owner of the boundary face (its low face along p)
+  int body;
+};
+
+template <typename T>
+struct Geo {
+  const T* q[G_NQ];
+};
+
+template <typename T>
+struct StageParams {
+  const CaseDev<T>* cases;
+  const BlockDev* blocks;
+  const int4* tiles;       // (block, i0, j0, k0)
+  int ntiles;
+  Geo<T> g;
+  const T* Uprev;          // halos filled
+  const T* U0;             // iteration start state (RK mode)
+  T* Unext;                // RK mode output
+  T* R;                    // residual mode output
+  double* partials;        // [ntiles][8] FP64 norm partials, or null
+  T alpha;                 // RK stage coefficient
+  int TI, TJ, ti_shift;    // tile shape; TI = 1 << ti_shift
+};
+
+template <typename T>
+struct HaloParams {
+  const CaseDev<T>* cases;
+  const BlockDev* blocks;
+  Geo<T> g;
+  T* U;
+  const CopyRec* copies;
+  int ncopy;
+  const BcRec* bcs;
+  int nbc;
+  int ns_max;
+};
+
+template <typename T>
+struct ForceParams {
+  const CaseDev<T>* cases;
+  const BlockDev* blocks;
+  Geo<T> g;
+  const T* U;               // halos filled
+  const BcRec* walls;
+  int nwall;
+  int ns;
+  double* face_out;         // [nwall][ns][3]
+  double* coef;             // [ns][nbodies][3] or null
+  double* J;                // or null
+  int nbodies;
+};
+
+// launchers (defined per precision in hb_kernels_f32.cu / hb_kernels_f64.cu)
+template <typename T>
+cudaError_t launch_halo(const HaloParams<T>& p, cudaStream_t s);
+template <typename T>
+cudaError_t launch_stage(const StageParams<T>& p, int ns, int viscous, int mode, cudaStream_t s);
+template <typename T>
+cudaError_t launch_init(const CaseDev<T>* cases, const BlockDev* blocks, int nblocks, Geo<T> g,
+                        T* U, const double* noise, double amp, int64_t total_interior,
+                        const int64_t* block_noff, cudaStream_t s);
+template <typename T>
+cudaError_t launch_forces(const ForceParams<T>& p, cudaStream_t s);
+template <typename T>
+cudaError_t stage_smem_bytes(int TI, int TJ, size_t* bytes);
+
+cudaError_t launch_norm_finish(const double* partials, int ntiles, int nv, double inv_count,
+                               double* out, int* err, cudaStream_t s);
+cudaError_t launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t s);
+
+}  // namespace hbk

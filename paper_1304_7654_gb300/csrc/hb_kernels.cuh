@@ -1,0 +1,725 @@
+// CUDA kernels of the HB residual path (sm_103a), templated on the
+// arithmetic type T (float or double).
+//
+// Method (the paper's HB NS solver, Sec. 1; per-RK-step cut exchange and
+// force reduction, Sec. 3.1), with the scheme readings:
+//   * primitives W = (rho, u, v, p); MUSCL W_L = W_{i-1} + s_{i-1}/2,
+//     W_R = W_i - s_i/2, slopes s = va(backward, forward) with the van Albada
+//     limiter va(a,b) = ((b^2+eps) a + (a^2+eps) b) / (a^2 + b^2 + 2 eps);
+//   * Roe flux with the grid velocity of a rigid pitch (relative normal
+//     velocity in the convective terms), Harten fix on the acoustic waves;
+//   * viscous flux: Green-Gauss cell gradients of (u, v, T), face gradient =
+//     mean + edge-normal correction, Stokes stress, Fourier heat flux;
+//   * HB source V * omega * sum_m D[n][m] U_m;
+//   * local time step CFL V / (sum_d (|u_rel . S_d| + c|S_d|) + viscous
+//     + omega N_H V), 4-stage RK U^(s) = U^(0) - alpha_s dtau/V R(U^(s-1)).
+//
+// Tile kernel layout: one CTA owns a TI x TJ tile of one block and loops over
+// all snapshots; per snapshot it stages the primitives of the tile plus a
+// 2-cell halo in shared memory, computes Green-Gauss gradients on a 1-cell
+// ring, then every face flux of the tile exactly once, and accumulates the
+// flux balance of each own cell into registers.  The HB source needs the own
+// cell at all snapshots: it is accumulated as each snapshot passes, so the
+// state is read once per stage.  Registers hold acc[NS][NV] (flux balance)
+// and h[NS][NV] (D.U) as shift registers indexed at compile time.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "hb_internal.h"
+
+namespace hbk {
+
+template <typename T>
+struct Fr {
+  T c, s, thd, px, py;
+};
+
+template <typename T>
+__device__ __forceinline__ Fr<T> frame_at(const CaseDev<T>* C, int n) {
+  Fr<T> f;
+  f.c = C->cth[n];
+  f.s = C->sth[n];
+  f.thd = C->thd[n];
+  f.px = C->pivot[0];
+  f.py = C->pivot[1];
+  return f;
+}
+
+template <typename T>
+__device__ __forceinline__ void rotv(const Fr<T>& f, T x, T y, T& ox, T& oy) {
+  ox = f.c * x - f.s * y;
+  oy = f.s * x + f.c * y;
+}
+
+template <typename T>
+__device__ __forceinline__ void rotp(const Fr<T>& f, T x, T y, T& ox, T& oy) {
+  T rx = x - f.px, ry = y - f.py;
+  ox = f.c * rx - f.s * ry + f.px;
+  oy = f.s * rx + f.c * ry + f.py;
+}
+
+template <typename T>
+__device__ __forceinline__ T van_albada(T a, T b, T eps) {
+  return ((b * b + eps) * a + (a * a + eps) * b) / (a * a + b * b + T(2) * eps);
+}
+
+// Roe flux through area vector (Sx, Sy) of a face moving with normal speed
+// vgn (grid velocity . unit normal).  W = (rho, u, v, p).  F = (mass, mx, my, E).
+template <typename T>
+__device__ __forceinline__ void roe2d(const T* WL, const T* WR, T Sx, T Sy, T vgn, T gam,
+                                      int efix, T efrac, T* F) {
+  const T A = sqrt(Sx * Sx + Sy * Sy);
+  const T nx = Sx / A, ny = Sy / A;
+  const T gm1 = gam - T(1);
+  const T qL = WL[1] * nx + WL[2] * ny;
+  const T qR = WR[1] * nx + WR[2] * ny;
+  const T kL = T(0.5) * (WL[1] * WL[1] + WL[2] * WL[2]);
+  const T kR = T(0.5) * (WR[1] * WR[1] + WR[2] * WR[2]);
+  const T HL = gam / gm1 * WL[3] / WL[0] + kL;
+  const T HR = gam / gm1 * WR[3] / WR[0] + kR;
+  const T r = sqrt(WR[0] / WL[0]);
+  const T rt = r * WL[0];
+  const T inv1r = T(1) / (T(1) + r);
+  const T ut = (WL[1] + r * WR[1]) * inv1r;
+  const T vt = (WL[2] + r * WR[2]) * inv1r;
+  const T Ht = (HL + r * HR) * inv1r;
+  const T kt = T(0.5) * (ut * ut + vt * vt);
+  const T ct2 = gm1 * (Ht - kt);
+  const T ct = sqrt(ct2);
+  const T qt = ut * nx + vt * ny;
+  const T qtr = qt - vgn;
+  T l1 = fabs(qtr - ct), l2 = fabs(qtr), l3 = fabs(qtr + ct);
+  if (efix) {
+    const T del = efrac * ct;
+    if (l1 < del) l1 = (l1 * l1 + del * del) / (T(2) * del);
+    if (l3 < del) l3 = (l3 * l3 + del * del) / (T(2) * del);
+  }
+  const T dp = WR[3] - WL[3], drho = WR[0] - WL[0], dq = qR - qL;
+  const T a1 = (dp - rt * ct * dq) / (T(2) * ct2);
+  const T a3 = (dp + rt * ct * dq) / (T(2) * ct2);
+  const T a2 = drho - dp / ct2;
+  const T dux = (WR[1] - WL[1]) - dq * nx;
+  const T duy = (WR[2] - WL[2]) - dq * ny;
+  const T udu = ut * dux + vt * duy;
+  const T w1 = l1 * a1, w3 = l3 * a3;
+  const T D0 = w1 + l2 * a2 + w3;
+  const T D1 = w1 * (ut - ct * nx) + l2 * (a2 * ut + rt * dux) + w3 * (ut + ct * nx);
+  const T D2 = w1 * (vt - ct * ny) + l2 * (a2 * vt + rt * duy) + w3 * (vt + ct * ny);
+  const T D3 = w1 * (Ht - ct * qt) + l2 * (a2 * kt + rt * udu) + w3 * (Ht + ct * qt);
+  const T qLr = qL - vgn, qRr = qR - vgn;
+  const T EL = WL[3] / gm1 + WL[0] * kL, ER = WR[3] / gm1 + WR[0] * kR;
+  const T hA = T(0.5) * A;
+  F[0] = hA * (WL[0] * qLr + WR[0] * qRr - D0);
+  F[1] = hA * (WL[0] * WL[1] * qLr + WL[3] * nx + WR[0] * WR[1] * qRr + WR[3] * nx - D1);
+  F[2] = hA * (WL[0] * WL[2] * qLr + WL[3] * ny + WR[0] * WR[2] * qRr + WR[3] * ny - D2);
+  F[3] = hA * (EL * qLr + WL[3] * qL + ER * qRr + WR[3] * qR - D3);
+}
+
+// Viscous flux through (Sx, Sy) from cell gradients gL, gR = (ux,uy,vx,vy,Tx,Ty),
+// cell values (u, v, T) and the rotated centre difference (tx, ty) = x_R - x_L.
+template <typename T>
+__device__ __forceinline__ void visc2d(const T* gL, const T* gR, T uL, T vL, T TL, T uR, T vR,
+                                       T TR, T tx, T ty, T Sx, T Sy, T mu, T kap, T* Fv) {
+  const T len = sqrt(tx * tx + ty * ty);
+  const T ex = tx / len, ey = ty / len;
+  T g[6];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const T bx = T(0.5) * (gL[2 * q] + gR[2 * q]);
+    const T by = T(0.5) * (gL[2 * q + 1] + gR[2 * q + 1]);
+    const T dphi = (q == 0) ? (uR - uL) : (q == 1) ? (vR - vL) : (TR - TL);
+    const T corr = dphi / len - (bx * ex + by * ey);
+    g[2 * q] = bx + corr * ex;
+    g[2 * q + 1] = by + corr * ey;
+  }
+  const T div = g[0] + g[3];
+  const T txx = mu * (T(2) * g[0]) - T(2.0 / 3.0) * mu * div;
+  const T tyy = mu * (T(2) * g[3]) - T(2.0 / 3.0) * mu * div;
+  const T txy = mu * (g[1] + g[2]);
+  const T fx = txx * Sx + txy * Sy;
+  const T fy = txy * Sx + tyy * Sy;
+  const T uf = T(0.5) * (uL + uR), vf = T(0.5) * (vL + vR);
+  Fv[0] = T(0);
+  Fv[1] = fx;
+  Fv[2] = fy;
+  Fv[3] = uf * fx + vf * fy + kap * (g[4] * Sx + g[5] * Sy);
+}
+
+template <typename T>
+__host__ __device__ constexpr size_t tile2d_smem_elems(int TI, int TJ) {
+  return (size_t)17 * (TI + 4) * (TJ + 4) + (size_t)6 * (TI + 2) * (TJ + 2) +
+         (size_t)4 * ((TI + 1) * TJ + TI * (TJ + 1));
+}
+
+// block-wide FP64 sum of up to 8 values, fixed order; result valid in thread 0
+__device__ __forceinline__ void block_sum8(double* v, int nv, double* scratch) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+  for (int q = 0; q < nv; ++q) {
+    double x = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) scratch[warp * 8 + q] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < nv; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < nwarp; ++w) s += scratch[w * 8 + q];
+      v[q] = s;
+    }
+  }
+}
+
+// MODE 0: R := residual.  MODE 1: RK stage update (+ norm partials if set).
+template <typename T, int NS, bool VISC, int MODE>
+__device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
+  constexpr int NV = 4;
+  const int4 tl = P.tiles[t];
+  const BlockDev B = P.blocks[tl.x];
+  const CaseDev<T>* C = P.cases + B.cs;
+  const int TI = P.TI, TJ = P.TJ;
+  const int RI = TI + 4, RJ = TJ + 4, NR = RI * RJ;
+  const int GI = TI + 2, NG = GI * (TJ + 2);
+  const int NFI = (TI + 1) * TJ, NF = NFI + TI * (TJ + 1);
+  const int i0 = tl.y, j0 = tl.z;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int P0 = B.P[0];
+  const int n0 = B.n[0], n1 = B.n[1];
+
+  T* sW = sm;              // [4][NR] primitives rho, u, v, p
+  T* sVol = sW + 4 * NR;   // [NR]
+  T* sDc = sVol + NR;      // [d*2+comp][NR] centre minus low-neighbour centre
+  T* sS = sDc + 4 * NR;    // [d*2+comp][NR]
+  T* sXf = sS + 4 * NR;    // [d*2+comp][NR]
+  T* sG = sXf + 4 * NR;    // [6][NG]
+  T* sF = sG + 6 * NG;     // [NV][NF]
+
+  const T gam = C->gamma, gm1 = C->gamma - T(1), eps = C->eps, efrac = C->ent_frac;
+  const T mu = C->mu, kap = C->kappa, omega = C->omega;
+  const int efix = C->entropy_fix;
+  const bool moving = C->motion != 0;
+
+  // ---- static geometry of the region (tile + 2-cell halo)
+  for (int r = tid; r < NR; r += nt) {
+    const int ri = r % RI, rj = r / RI;
+    const int i = i0 - 2 + ri, j = j0 - 2 + rj;
+    if (i <= n0 + 1 && j <= n1 + 1) {
+      const int64_t c = B.goff + (int64_t)(j + 2) * P0 + (i + 2);
+      sVol[r] = P.g.q[G_VOL][c];
+      sDc[r] = P.g.q[G_DC + 0][c];
+      sDc[NR + r] = P.g.q[G_DC + 1][c];
+      sDc[2 * NR + r] = P.g.q[G_DC + 3][c];
+      sDc[3 * NR + r] = P.g.q[G_DC + 4][c];
+      sS[r] = P.g.q[G_S + 0][c];
+      sS[NR + r] = P.g.q[G_S + 1][c];
+      sS[2 * NR + r] = P.g.q[G_S + 3][c];
+      sS[3 * NR + r] = P.g.q[G_S + 4][c];
+      if (moving) {
+        sXf[r] = P.g.q[G_XF + 0][c];
+        sXf[NR + r] = P.g.q[G_XF + 1][c];
+        sXf[2 * NR + r] = P.g.q[G_XF + 3][c];
+        sXf[3 * NR + r] = P.g.q[G_XF + 4][c];
+      }
+    } else {   // outside the padded block: benign unit cell, never used by own cells
+      sVol[r] = T(1);
+      sDc[r] = T(1);
+      sDc[NR + r] = T(0);
+      sDc[2 * NR + r] = T(0);
+      sDc[3 * NR + r] = T(1);
+      sS[r] = T(1);
+      sS[NR + r] = T(0);
+      sS[2 * NR + r] = T(0);
+      sS[3 * NR + r] = T(1);
+      sXf[r] = T(0);
+      sXf[NR + r] = T(0);
+      sXf[2 * NR + r] = T(0);
+      sXf[3 * NR + r] = T(0);
+    }
+  }
+
+  const int ti = tid & (TI - 1), tj = tid >> P.ti_shift;
+  const int ci = i0 + ti, cj = j0 + tj;
+  const bool own = (tid < TI * TJ) && ci < n0 && cj < n1;
+  const int rown = (tj + 2) * RI + (ti + 2);
+  const int64_t cown = (int64_t)(cj + 2) * P0 + (ci + 2);
+
+  T acc[NS][NV], h[NS][NV];
+#pragma unroll
+  for (int m = 0; m < NS; ++m)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) { acc[m][v] = T(0); h[m][v] = T(0); }
+
+  for (int n = 0; n < NS; ++n) {
+    const Fr<T> f = frame_at(C, n);
+    __syncthreads();
+    // ---- primitives of the region at snapshot n
+    for (int r = tid; r < NR; r += nt) {
+      const int ri = r % RI, rj = r / RI;
+      const int i = i0 - 2 + ri, j = j0 - 2 + rj;
+      T w0 = T(1), w1 = T(0), w2 = T(0), w3 = T(1);
+      if (i <= n0 + 1 && j <= n1 + 1) {
+        const T* u = P.Uprev + B.off + (int64_t)n * NV * B.plane + (int64_t)(j + 2) * P0 + (i + 2);
+        const T rho = u[0], mx = u[B.plane], my = u[2 * B.plane], E = u[3 * B.plane];
+        w0 = rho;
+        w1 = mx / rho;
+        w2 = my / rho;
+        w3 = gm1 * (E - T(0.5) * rho * (w1 * w1 + w2 * w2));
+      }
+      sW[r] = w0;
+      sW[NR + r] = w1;
+      sW[2 * NR + r] = w2;
+      sW[3 * NR + r] = w3;
+    }
+    __syncthreads();
+    // ---- Green-Gauss gradients of (u, v, T) on the 1-cell ring
+    if (VISC) {
+      for (int gq = tid; gq < NG; gq += nt) {
+        const int gi = gq % GI, gj = gq / GI;
+        const int r = (gj + 1) * RI + (gi + 1);
+        // Green-Gauss with face values (phi_c + phi_nb)/2 over a closed cell,
+        // written as sum (phi_nb - phi_c)/2 S (the faces sum to zero), which
+        // keeps the rounding of large face vectors out of small cells
+        const T uc = sW[NR + r], vc = sW[2 * NR + r], Tc = gam * sW[3 * NR + r] / sW[r];
+        T g[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        const int nb[4] = {r - 1, r + 1, r - RI, r + RI};
+        const int fo[4] = {r, r + 1, r, r + RI};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int d = k >> 1;
+          const T sg = (k & 1) ? T(1) : T(-1);
+          T sx, sy;
+          rotv(f, sS[(2 * d) * NR + fo[k]], sS[(2 * d + 1) * NR + fo[k]], sx, sy);
+          sx *= sg;
+          sy *= sg;
+          const int o = nb[k];
+          const T un = sW[NR + o], vn = sW[2 * NR + o], Tn = gam * sW[3 * NR + o] / sW[o];
+          const T fu = T(0.5) * (un - uc), fv = T(0.5) * (vn - vc), fT = T(0.5) * (Tn - Tc);
+          g[0] += fu * sx; g[1] += fu * sy;
+          g[2] += fv * sx; g[3] += fv * sy;
+          g[4] += fT * sx; g[5] += fT * sy;
+        }
+        const T iv = T(1) / sVol[r];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) sG[q * NG + gq] = g[q] * iv;
+      }
+      __syncthreads();
+    }
+    // ---- every face of the tile once
+    for (int fq = tid; fq < NF; fq += nt) {
+      int rL, st, d, gLi, gRi;
+      if (fq < NFI) {
+        const int fi = fq % (TI + 1), fj = fq / (TI + 1);
+        rL = (fj + 2) * RI + (fi + 1);
+        st = 1;
+        d = 0;
+        gLi = (fj + 1) * GI + fi;
+        gRi = gLi + 1;
+      } else {
+        const int g2 = fq - NFI;
+        const int fi = g2 % TI, fj = g2 / TI;
+        rL = (fj + 1) * RI + (fi + 2);
+        st = RI;
+        d = 1;
+        gLi = fj * GI + fi + 1;
+        gRi = gLi + GI;
+      }
+      const int rR = rL + st;
+      T WL[4], WR[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T a = sW[q * NR + rL - st], b = sW[q * NR + rL], c = sW[q * NR + rR],
+                dd = sW[q * NR + rR + st];
+        WL[q] = b + T(0.5) * van_albada(b - a, c - b, eps);
+        WR[q] = c - T(0.5) * van_albada(c - b, dd - c, eps);
+      }
+      T sx, sy;
+      rotv(f, sS[(2 * d) * NR + rR], sS[(2 * d + 1) * NR + rR], sx, sy);
+      T vgn = T(0);
+      if (moving) {
+        T xf, yf;
+        rotp(f, sXf[(2 * d) * NR + rR], sXf[(2 * d + 1) * NR + rR], xf, yf);
+        const T vgx = -f.thd * (yf - f.py), vgy = f.thd * (xf - f.px);
+        vgn = (vgx * sx + vgy * sy) / sqrt(sx * sx + sy * sy);
+      }
+      T F[4];
+      roe2d(WL, WR, sx, sy, vgn, gam, efix, efrac, F);
+      if (VISC) {
+        T gl[6], gr[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) { gl[q] = sG[q * NG + gLi]; gr[q] = sG[q * NG + gRi]; }
+        T tx, ty;
+        rotv(f, sDc[(2 * d) * NR + rR], sDc[(2 * d + 1) * NR + rR], tx, ty);
+        const T TL = gam * sW[3 * NR + rL] / sW[rL], TR = gam * sW[3 * NR + rR] / sW[rR];
+        T Fv[4];
+        visc2d(gl, gr, sW[NR + rL], sW[2 * NR + rL], TL, sW[NR + rR], sW[2 * NR + rR], TR, tx, ty,
+               sx, sy, mu, kap, Fv);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) F[q] -= Fv[q];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sF[q * NF + fq] = F[q];
+    }
+    __syncthreads();
+    if (own) {
+      const int fi0 = tj * (TI + 1) + ti;
+      const int fj0 = NFI + tj * TI + ti;
+      T Rn[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q)
+        Rn[q] = (sF[q * NF + fi0 + 1] - sF[q * NF + fi0]) + (sF[q * NF + fj0 + TI] - sF[q * NF + fj0]);
+#pragma unroll
+      for (int m = 0; m < NS - 1; ++m)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[m][q] = acc[m + 1][q];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) acc[NS - 1][q] = Rn[q];
+      const T* u = P.Uprev + B.off + (int64_t)n * NV * B.plane + cown;
+      T uc[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) uc[q] = u[q * B.plane];
+#pragma unroll
+      for (int m = 0; m < NS; ++m) {
+        const T dmn = C->D[m * NS + n];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) h[m][q] += dmn * uc[q];
+      }
+    }
+  }
+
+  // ---- epilogue: HB source, residual or RK update, norm partials
+  // norm partials: squares summed over this cell's snapshots in T, then
+  // accumulated across cells and CTAs in FP64
+  T tacc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) tacc[q] = T(0);
+  double nacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (own) {
+    const T V = sVol[rown];
+    const T vw = V * omega;
+    for (int n = 0; n < NS; ++n) {
+      T Rn[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) Rn[q] = acc[0][q] + vw * h[0][q];
+      const int64_t base = B.off + (int64_t)n * NV * B.plane + cown;
+      if (MODE == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) P.R[base + q * B.plane] = Rn[q];
+      } else {
+        T u0[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) u0[q] = P.U0[base + q * B.plane];
+        const Fr<T> f = frame_at(C, n);
+        const T rho = u0[0], uu = u0[1] / rho, vv = u0[2] / rho;
+        const T pp = gm1 * (u0[3] - T(0.5) * rho * (uu * uu + vv * vv));
+        const T cs = sqrt(gam * pp / rho);
+        T urx = uu, ury = vv;
+        if (moving) {
+          T xc, yc;
+          rotp(f, P.g.q[G_XC][B.goff + cown], P.g.q[G_XC + 1][B.goff + cown], xc, yc);
+          urx -= -f.thd * (yc - f.py);
+          ury -= f.thd * (xc - f.px);
+        }
+        T ax, ay, bx, by;
+        rotv(f, T(0.5) * (sS[rown] + sS[rown + 1]), T(0.5) * (sS[NR + rown] + sS[NR + rown + 1]), ax, ay);
+        rotv(f, T(0.5) * (sS[2 * NR + rown] + sS[2 * NR + rown + RI]),
+             T(0.5) * (sS[3 * NR + rown] + sS[3 * NR + rown + RI]), bx, by);
+        const T ma2 = ax * ax + ay * ay, mb2 = bx * bx + by * by;
+        T lam = fabs(urx * ax + ury * ay) + cs * sqrt(ma2) + fabs(urx * bx + ury * by) + cs * sqrt(mb2);
+        if (VISC) {
+          const T cv = (gam / C->prandtl > T(4.0 / 3.0)) ? gam / C->prandtl : T(4.0 / 3.0);
+          lam += T(4) * cv * (mu / rho) * (ma2 + mb2) / V;
+        }
+        lam += omega * T(C->nh) * V;
+        const T dtau = C->cfl * V / lam;
+        const T fac = P.alpha * dtau / V;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) P.Unext[base + q * B.plane] = u0[q] - fac * Rn[q];
+        if (P.partials) {
+          const T iV = T(1) / V;
+#pragma unroll
+          for (int q = 0; q < NV; ++q) {
+            const T x = Rn[q] * iV;
+            tacc[q] += x * x;
+          }
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < NS - 1; ++m)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) { acc[m][q] = acc[m + 1][q]; h[m][q] = h[m + 1][q]; }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) nacc[q] = (double)tacc[q];
+  if (MODE == 1 && P.partials) {
+    __syncthreads();
+    double* scratch = reinterpret_cast<double*>(sm);   // primitives are dead here
+    block_sum8(nacc, NV, scratch);
+    if (threadIdx.x == 0)
+      for (int q = 0; q < NV; ++q) P.partials[(int64_t)t * 8 + q] = nacc[q];
+  }
+}
+
+template <typename T, int NS, bool VISC, int MODE>
+__global__ void __launch_bounds__(MAXNT) tile2d_kernel(StageParams<T> P) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  tile2d<T, NS, VISC, MODE>(P, blockIdx.x, reinterpret_cast<T*>(smraw));
+}
+
+// ------------------------------------------------------------- halos/BCs --
+template <typename T>
+__device__ __forceinline__ void freestream_at(const CaseDev<T>* C, int n, T x, T* W) {
+  W[0] = C->winf[n][0];
+  W[1] = C->winf[n][1];
+  W[2] = C->winf[n][2];
+  W[3] = C->winf[n][3];
+  W[4] = C->winf[n][4];
+  if (C->ubc == 2) W[2] += C->ubc_amp * C->mach * sin(C->tn[n] - C->omega * x / C->mach);
+}
+
+// one thread per (record, snapshot), snapshot-major so that neighbouring
+// threads touch neighbouring cells
+template <typename T, int DIM>
+__global__ void halo_kernel(HaloParams<T> p) {
+  constexpr int NV = DIM + 2;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nc = (int64_t)p.ncopy * p.ns_max;
+  if (gid < nc) {
+    const int n = (int)(gid / p.ncopy), rec = (int)(gid % p.ncopy);
+    const CopyRec r = p.copies[rec];
+    const BlockDev& D = p.blocks[r.dst_blk];
+    const BlockDev& S = p.blocks[r.src_blk];
+    if (n >= p.cases[D.cs].ns) return;
+    const T* src = p.U + S.off + (int64_t)n * NV * S.plane + r.src_cell;
+    T* dst = p.U + D.off + (int64_t)n * NV * D.plane + r.dst_cell;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dst[v * D.plane] = src[v * S.plane];
+    return;
+  }
+  const int64_t gb = gid - nc;
+  if (gb >= (int64_t)p.nbc * p.ns_max) return;
+  const int n = (int)(gb / p.nbc), rec = (int)(gb % p.nbc);
+  const BcRec r = p.bcs[rec];
+  const BlockDev& B = p.blocks[r.blk];
+  const CaseDev<T>* C = p.cases + B.cs;
+  if (n >= C->ns) return;
+  const Fr<T> f = frame_at(C, n);
+  const T gam = C->gamma, gm1 = gam - T(1);
+  const int64_t fc = B.goff + r.fcell;
+  T S[3] = {p.g.q[G_S + 3 * r.p][fc], p.g.q[G_S + 3 * r.p + 1][fc], T(0)};
+  T X[3] = {p.g.q[G_XF + 3 * r.p][fc], p.g.q[G_XF + 3 * r.p + 1][fc], T(0)};
+  if (DIM == 3) {
+    S[2] = p.g.q[G_S + 3 * r.p + 2][fc];
+    X[2] = p.g.q[G_XF + 3 * r.p + 2][fc];
+  }
+  T sr[3], xr[3];
+  rotv(f, S[0], S[1], sr[0], sr[1]);
+  sr[2] = S[2];
+  rotp(f, X[0], X[1], xr[0], xr[1]);
+  xr[2] = X[2];
+  const T vg[3] = {-f.thd * (xr[1] - f.py), f.thd * (xr[0] - f.px), T(0)};
+  const T A = sqrt(sr[0] * sr[0] + sr[1] * sr[1] + sr[2] * sr[2]);
+  const T sg = T(r.sgn);
+  const T nr[3] = {sg * sr[0] / A, sg * sr[1] / A, sg * sr[2] / A};
+  T* Ub = p.U + B.off + (int64_t)n * NV * B.plane;
+  auto load = [&](int cell, T* W) {
+    const T rho = Ub[cell];
+    W[0] = rho;
+    W[1] = Ub[B.plane + cell] / rho;
+    W[2] = Ub[2 * B.plane + cell] / rho;
+    W[3] = (DIM == 3) ? Ub[3 * B.plane + cell] / rho : T(0);
+    W[4] = gm1 * (Ub[(NV - 1) * B.plane + cell] - T(0.5) * rho * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]));
+  };
+  auto store = [&](int cell, const T* W) {
+    Ub[cell] = W[0];
+    Ub[B.plane + cell] = W[0] * W[1];
+    Ub[2 * B.plane + cell] = W[0] * W[2];
+    if (DIM == 3) Ub[3 * B.plane + cell] = W[0] * W[3];
+    Ub[(NV - 1) * B.plane + cell] = W[4] / gm1 + T(0.5) * W[0] * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+  };
+  if (r.type == 1) {   // characteristic farfield (Riemann invariants normal to the face)
+    T Wi[5], Wf[5];
+    load(r.mcell[0], Wi);
+    freestream_at(C, n, xr[0], Wf);
+    const T qi = (Wi[1] - vg[0]) * nr[0] + (Wi[2] - vg[1]) * nr[1] + (Wi[3] - vg[2]) * nr[2];
+    const T qf = (Wf[1] - vg[0]) * nr[0] + (Wf[2] - vg[1]) * nr[1] + (Wf[3] - vg[2]) * nr[2];
+    const T ci = sqrt(gam * Wi[4] / Wi[0]), cf = sqrt(gam * Wf[4] / Wf[0]);
+    const T Rp = qi + T(2) * ci / gm1, Rm = qf - T(2) * cf / gm1;
+    const T qb = T(0.5) * (Rp + Rm);
+    const T cb = T(0.25) * gm1 * (Rp - Rm);
+    const T* Wr = (qb > T(0)) ? Wi : Wf;
+    const T qr = (qb > T(0)) ? qi : qf;
+    const T ent = Wr[4] / pow(Wr[0], gam);
+    T Wg[5];
+    Wg[0] = pow(cb * cb / (gam * ent), T(1) / gm1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Wg[1 + a] = vg[a] + ((Wr[1 + a] - vg[a]) - qr * nr[a]) + qb * nr[a];
+    if (DIM == 2) Wg[3] = T(0);
+    Wg[4] = Wg[0] * cb * cb / gam;
+    store(r.gcell[0], Wg);
+    store(r.gcell[1], Wg);
+  } else {
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      T Wm[5], Wg[5];
+      load(r.mcell[l], Wm);
+      Wg[0] = Wm[0];
+      Wg[4] = Wm[4];
+      if (r.type == 2) {   // slip wall: reflect the relative normal velocity
+        const T qn = (Wm[1] - vg[0]) * nr[0] + (Wm[2] - vg[1]) * nr[1] + (Wm[3] - vg[2]) * nr[2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) Wg[1 + a] = Wm[1 + a] - T(2) * qn * nr[a];
+      } else {             // no-slip adiabatic wall: u_g = 2 v_wall - u
+#pragma unroll
+        for (int a = 0; a < 3; ++a) Wg[1 + a] = T(2) * vg[a] - Wm[1 + a];
+      }
+      if (DIM == 2) Wg[3] = T(0);
+      store(r.gcell[l], Wg);
+    }
+  }
+}
+
+// ---------------------------------------------------------- initial state --
+template <typename T, int DIM>
+__global__ void init_kernel(const CaseDev<T>* cases, const BlockDev* blocks, Geo<T> g, T* U,
+                            const double* noise, double amp, int blk) {
+  constexpr int NV = DIM + 2;
+  const BlockDev B = blocks[blk];
+  const CaseDev<T>* C = cases + B.cs;
+  const int64_t ncell = (int64_t)B.n[0] * B.n[1] * B.n[2];
+  const int64_t tot = ncell * C->ns * NV;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cellid = e % ncell;
+    const int v = (int)((e / ncell) % NV);
+    const int n = (int)(e / (ncell * NV));
+    const int i = (int)(cellid % B.n[0]);
+    const int j = (int)((cellid / B.n[0]) % B.n[1]);
+    const int k = (int)(cellid / ((int64_t)B.n[0] * B.n[1]));
+    const int64_t c = ((int64_t)(k + B.gk) * B.P[1] + (j + 2)) * B.P[0] + (i + 2);
+    T W[5];
+    freestream_at(C, n, g.q[G_XC][B.goff + c], W);
+    T val;
+    if (v == 0) val = W[0];
+    else if (v <= DIM) val = W[0] * W[v];
+    else val = W[4] / (C->gamma - T(1)) + T(0.5) * W[0] * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+    const double z = noise ? noise[B.noff + e] : 0.0;
+    U[B.off + ((int64_t)n * NV + v) * B.plane + c] = (T)((double)val * (1.0 + amp * z));
+  }
+}
+
+// ----------------------------------------------------------------- forces --
+// Green-Gauss gradient of (u, v, T) at padded cell c from global memory (2D)
+template <typename T>
+__device__ void grad_global2d(const BlockDev& B, const CaseDev<T>* C, const Geo<T>& g,
+                              const T* Ub, const Fr<T>& f, int c, T* out) {
+  const T gam = C->gamma, gm1 = gam - T(1);
+  auto prim = [&](int cc, T& u, T& v, T& Tt) {
+    const T rho = Ub[cc];
+    u = Ub[B.plane + cc] / rho;
+    v = Ub[2 * B.plane + cc] / rho;
+    const T p = gm1 * (Ub[3 * B.plane + cc] - T(0.5) * rho * (u * u + v * v));
+    Tt = gam * p / rho;
+  };
+  T uc, vc, Tc;
+  prim(c, uc, vc, Tc);
+  const int P0 = B.P[0];
+  const int nb[4] = {c - 1, c + 1, c - P0, c + P0};
+  const int fo[4] = {c, c + 1, c, c + P0};
+  for (int q = 0; q < 6; ++q) out[q] = T(0);
+  for (int k = 0; k < 4; ++k) {
+    const int d = k >> 1;
+    const T sg = (k & 1) ? T(1) : T(-1);
+    T sx, sy;
+    rotv(f, g.q[G_S + 3 * d][B.goff + fo[k]], g.q[G_S + 3 * d + 1][B.goff + fo[k]], sx, sy);
+    T un, vn, Tn;
+    prim(nb[k], un, vn, Tn);
+    const T fu = T(0.5) * (un - uc), fv = T(0.5) * (vn - vc), fT = T(0.5) * (Tn - Tc);
+    out[0] += sg * fu * sx; out[1] += sg * fu * sy;
+    out[2] += sg * fv * sx; out[3] += sg * fv * sy;
+    out[4] += sg * fT * sx; out[5] += sg * fT * sy;
+  }
+  const T iv = T(1) / g.q[G_VOL][B.goff + c];
+  for (int q = 0; q < 6; ++q) out[q] *= iv;
+}
+
+// per wall face and snapshot: pressure and viscous force, moment about the pivot
+template <typename T>
+__global__ void force_faces_kernel(ForceParams<T> p) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= p.nwall * p.ns) return;
+  const int rec = gid / p.ns, n = gid % p.ns;
+  const BcRec r = p.walls[rec];
+  const BlockDev B = p.blocks[r.blk];
+  const CaseDev<T>* C = p.cases + B.cs;
+  const Fr<T> f = frame_at(C, n);
+  const T gam = C->gamma, gm1 = gam - T(1);
+  const T* Ub = p.U + B.off + (int64_t)n * 4 * B.plane;
+  const int64_t fc = B.goff + r.fcell;
+  T sx, sy, xf, yf;
+  rotv(f, p.g.q[G_S + 3 * r.p][fc], p.g.q[G_S + 3 * r.p + 1][fc], sx, sy);
+  rotp(f, p.g.q[G_XF + 3 * r.p][fc], p.g.q[G_XF + 3 * r.p + 1][fc], xf, yf);
+  const T sg = T(r.sgn);
+  const T sbx = sg * sx, sby = sg * sy;   // into the body
+  const int ic = r.mcell[0], gc = r.gcell[0];
+  const T rho = Ub[ic], u = Ub[B.plane + ic] / rho, v = Ub[2 * B.plane + ic] / rho;
+  const T pw = gm1 * (Ub[3 * B.plane + ic] - T(0.5) * rho * (u * u + v * v));
+  T Fx = (pw - C->pinf) * sbx, Fy = (pw - C->pinf) * sby;
+  if (C->viscous) {
+    const int cl = (r.sgn > 0) ? ic : gc, cr = (r.sgn > 0) ? gc : ic;
+    T gL[6], gR[6];
+    grad_global2d(B, C, p.g, Ub, f, cl, gL);
+    grad_global2d(B, C, p.g, Ub, f, cr, gR);
+    T tx, ty;   // centre difference x_R - x_L, stored with the high cell cr = cl + e_p
+    rotv(f, p.g.q[G_DC + 3 * r.p][B.goff + cr], p.g.q[G_DC + 3 * r.p + 1][B.goff + cr], tx, ty);
+    auto prim = [&](int cc, T& uu, T& vv, T& Tt) {
+      const T rr = Ub[cc];
+      uu = Ub[B.plane + cc] / rr;
+      vv = Ub[2 * B.plane + cc] / rr;
+      Tt = gam * gm1 * (Ub[3 * B.plane + cc] - T(0.5) * rr * (uu * uu + vv * vv)) / rr;
+    };
+    T uL, vL, TL, uR, vR, TR;
+    prim(cl, uL, vL, TL);
+    prim(cr, uR, vR, TR);
+    // traction through the face vector (pointing L -> R): reuse the flux routine
+    T Fv[4];
+    visc2d(gL, gR, uL, vL, TL, uR, vR, TR, tx, ty, sx, sy, C->mu, C->kappa, Fv);
+    // Fv[1..2] = tau . S with S = sgn * S_b; tau . S_b = sgn * Fv
+    Fx -= sg * Fv[1];
+    Fy -= sg * Fv[2];
+  }
+  const double q = 0.5 * (double)C->mach * (double)C->mach;
+  double* o = p.face_out + ((int64_t)rec * p.ns + n) * 3;
+  o[0] = ((double)Fx * (double)-C->sina0 + (double)Fy * (double)C->cosa0) / q;
+  o[1] = ((double)Fx * (double)C->cosa0 + (double)Fy * (double)C->sina0) / q;
+  o[2] = (C->functag == 3)
+             ? (((double)xf - (double)C->pivot[0]) * (double)Fy - ((double)yf - (double)C->pivot[1]) * (double)Fx) / q
+             : 0.0;
+}
+
+// fixed-order FP64 sums per (snapshot, body, component), then J
+template <typename T>
+__global__ void force_finish_kernel(ForceParams<T> p) {
+  extern __shared__ double fsm[];
+  const int tot = p.ns * p.nbodies * 3;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int k = e % 3, b = (e / 3) % p.nbodies, n = e / (3 * p.nbodies);
+    double s = 0.0;
+    for (int rec = 0; rec < p.nwall; ++rec)
+      if (p.walls[rec].body == b) s += p.face_out[((int64_t)rec * p.ns + n) * 3 + k];
+    fsm[e] = s;
+    if (p.coef) p.coef[e] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && p.J) {
+    double j = 0.0;
+    for (int n = 0; n < p.ns; ++n)
+      for (int b = 0; b < p.nbodies; ++b) j += fsm[(n * p.nbodies + b) * 3];
+    *p.J = j / (double)p.ns;
+  }
+}
+
+}  // namespace hbk

@@ -1,0 +1,207 @@
+"""GPU parity: libhb.so (through the C ABI) against the FP64 oracle.
+
+Tolerance (the residual reading of "1e-12 relative per residual component"):
+|R_gpu - R_oracle| <= tol * (sum over the cell's faces of |face flux| + |HB
+source|), the magnitude the residual cancels, per cell, variable and
+snapshot.  tol = 1e-12 for the FP64 path and 1e-5 for the FP32 flux path.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle.hb_oracle import Oracle
+from paper_1304_7654_gb300 import cases as C
+from paper_1304_7654_gb300 import hb
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+
+
+def _periodic_multiblock(**kw):
+    specs = [C.BlockSpec((0, 0), (10, 7)), C.BlockSpec((10, 0), (16, 7)),
+             C.BlockSpec((0, 7), (5, 12)), C.BlockSpec((5, 7), (16, 12), flip=True)]
+    return C.periodic_box2d(16, 12, specs=specs, **kw)
+
+
+CASES = {
+    "euler_channel_64x32": lambda: C.channel(),
+    "channel_ragged_37x11_steady": lambda: C.channel(37, 11, n_harm=0),
+    "channel_flip_viscous": lambda: C.channel(16, 8, viscous=True, blocks=[
+        C.BlockSpec((0, 0), (9, 8)), C.BlockSpec((9, 0), (16, 3), flip=True), C.BlockSpec((9, 3), (16, 8))]),
+    "ns_ogrid8_small": lambda: C.ns_ogrid8(128, 24, n_harm=3),
+    "periodic_multiblock_ns": lambda: _periodic_multiblock(viscous=True, n_harm=2),
+    "adjoint_ogrid4_small": lambda: C.adjoint_ogrid4(64, 16),
+    "thin_blocks": lambda: C.ogrid(40, 6, n_harm=1, specs=[
+        C.BlockSpec((0, 0), (1, 6)), C.BlockSpec((1, 0), (3, 6)), C.BlockSpec((3, 0), (40, 3)),
+        C.BlockSpec((3, 3), (40, 6))]),
+}
+
+
+def _setup(cs, prec, seed=None, amp=0.01):
+    o = Oracle(cs)
+    U = o.init_state(C.noise(cs, seed), amp)
+    ctx = hb.HBContext(cs, prec)
+    Ug = ctx.from_compact(torch.as_tensor(o.unpack(U), device="cuda"))
+    return o, U, ctx, Ug
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_residual_parity(name, prec):
+    cs = CASES[name]()
+    o, U, ctx, Ug = _setup(cs, prec)
+    if prec == "fp32":       # compare against the oracle on the FP32-rounded state
+        U = o.pack(ctx.to_compact(Ug).double().cpu().numpy())
+    Rref, sc = o.residual(U)
+    R = ctx.to_compact(ctx.residual(Ug)).double().cpu().numpy()
+    err = np.abs(R - o.unpack(Rref)) / o.unpack(sc)
+    assert err.max() < TOL[prec], (name, prec, err.max())
+    assert ctx.sync_status() == hb.HB_OK
+
+
+@pytest.mark.parametrize("name", ["euler_channel_64x32", "ns_ogrid8_small", "periodic_multiblock_ns",
+                                  "thin_blocks", "channel_flip_viscous"])
+def test_halo_exchange_matches_oracle_on_every_padded_cell(name):
+    cs = CASES[name]()
+    o, U, ctx, Ug = _setup(cs, "fp64")
+    Uf = o.fill_ghosts(U)
+    ctx.exchange_halos(Ug)
+    G = Ug.cpu().numpy()
+    for b, blk in enumerate(cs.blocks):
+        off, st, _ = ctx.layouts[b]
+        ni, nj, _ = blk.n
+        n = np.arange(cs.n_snap)[:, None, None, None]
+        v = np.arange(cs.nv)[None, :, None, None]
+        j = np.arange(nj + 4)[None, None, :, None]
+        i = np.arange(ni + 4)[None, None, None, :]
+        got = G[off + n * st[0] + v * st[1] + j * st[3] + i * st[4]]
+        ref = o.block_view(Uf, b)[:, :, 0]
+        assert np.allclose(got, ref, rtol=1e-14, atol=1e-15), (name, b, np.abs(got - ref).max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_init_state_matches_oracle(prec):
+    cs = C.ns_ogrid8(64, 24, n_harm=3)
+    o = Oracle(cs)
+    z = C.noise(cs)
+    U = o.init_state(z, 0.01)
+    ctx = hb.HBContext(cs, prec)
+    Ug = ctx.new_state()
+    ctx.init_state(Ug, torch.as_tensor(z, device="cuda"), 0.01)
+    got = ctx.to_compact(Ug).double().cpu().numpy()
+    tol = 1e-15 if prec == "fp64" else 1e-7
+    assert np.allclose(got, o.unpack(U), rtol=tol, atol=tol)
+
+
+def test_rk_trajectory_parity_config1_200_iterations():
+    cs = C.channel()
+    o, U, ctx, Ug = _setup(cs, "fp64")
+    Uo, no = o.rk_smooth(U, 200)
+    ng = ctx.rk_smooth(Ug, 200).cpu().numpy()
+    assert ctx.sync_status() == hb.HB_OK
+    Ugc = ctx.to_compact(Ug).cpu().numpy()
+    assert np.abs(Ugc - o.unpack(Uo)).max() < 1e-12 * np.abs(o.unpack(Uo)).max()
+    assert np.allclose(ng, no, rtol=1e-10, atol=0)
+    # and the residual of the final state, per component
+    Rref, sc = o.residual(Uo)
+    R = ctx.to_compact(ctx.residual(Ug)).cpu().numpy()
+    assert (np.abs(R - o.unpack(Rref)) / o.unpack(sc)).max() < 1e-12
+
+
+@pytest.mark.parametrize("name", ["ns_ogrid8_small", "periodic_multiblock_ns", "adjoint_ogrid4_small"])
+def test_rk_trajectory_parity_short(name):
+    cs = CASES[name]()
+    o, U, ctx, Ug = _setup(cs, "fp64")
+    Uo, no = o.rk_smooth(U, 10)
+    ng = ctx.rk_smooth(Ug, 10).cpu().numpy()
+    Ugc = ctx.to_compact(Ug).cpu().numpy()
+    assert np.abs(Ugc - o.unpack(Uo)).max() < 1e-12 * np.abs(o.unpack(Uo)).max()
+    assert np.allclose(ng, no, rtol=1e-10, atol=0)
+
+
+def test_fp32_rk_trajectory_error_is_bounded():
+    """FP32 flux path, 200 RK iterations of the 64x32 channel from the same
+    (FP32-rounded) start: measured state error 1.3e-5 of max|U|, bound 5e-5."""
+    cs = C.channel()
+    o, U, ctx, Ug = _setup(cs, "fp32")
+    U = o.pack(ctx.to_compact(Ug).double().cpu().numpy())
+    Uo, no = o.rk_smooth(U, 200)
+    ng = ctx.rk_smooth(Ug, 200).cpu().numpy()
+    Ugc = ctx.to_compact(Ug).double().cpu().numpy()
+    rel = np.abs(Ugc - o.unpack(Uo)).max() / np.abs(o.unpack(Uo)).max()
+    assert rel < 5e-5, rel
+    assert np.allclose(ng, no, rtol=1e-3), (ng[-1], no[-1])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_forces_parity(prec):
+    cs = C.ns_ogrid8(128, 24, n_harm=3)
+    o, U, ctx, Ug = _setup(cs, prec)
+    U, _ = o.rk_smooth(U, 5)
+    Ug = ctx.from_compact(torch.as_tensor(o.unpack(U), device="cuda"))
+    if prec == "fp32":
+        U = o.pack(ctx.to_compact(Ug).double().cpu().numpy())
+    cref, Jref = o.forces(U)
+    coef, J = ctx.forces(Ug)
+    coef = coef.cpu().numpy()
+    scale = np.abs(cref).max()
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    assert np.abs(coef - cref).max() < tol * scale, (np.abs(coef - cref).max(), scale)
+    assert abs(J.item() - Jref) < tol * scale
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_ns_ogrid8_sampled_residual(prec):
+    """Full 245,760-cell, 8-block, N_H = 3 workload: sampled cells (random plus
+    block corners, T-junctions and wall cells) against the oracle one by one."""
+    cs = C.ns_ogrid8()
+    o, U, ctx, Ug = _setup(cs, prec)
+    if prec == "fp32":
+        U = o.pack(ctx.to_compact(Ug).double().cpu().numpy())
+    cells = list(C.sample_cells(cs, 150, 21))
+    for b, blk in enumerate(cs.blocks):
+        ni, nj, _ = blk.n
+        for (i, j) in [(0, 0), (ni - 1, 0), (0, nj - 1), (ni - 1, nj - 1), (1, 1), (ni // 2, 0)]:
+            cells.append([b, i, j, 0])
+    cells = np.array(cells, dtype=np.int32)
+    Rref, sc = o.residual_cells(U, cells)
+    R = ctx.residual(Ug).double().cpu().numpy()
+    got = np.zeros_like(Rref)
+    for q, (b, i, j, k) in enumerate(cells):
+        off, st, _ = ctx.layouts[b]
+        for n in range(cs.n_snap):
+            for v in range(cs.nv):
+                got[q, n, v] = R[off + n * st[0] + v * st[1] + (j + 2) * st[3] + (i + 2)]
+    err = np.abs(got - Rref) / sc
+    assert err.max() < TOL[prec], err.max()
+
+
+def test_rk_is_bitwise_deterministic_and_graph_equals_direct():
+    cs = C.ns_ogrid8(128, 24, n_harm=3)
+    o, U, ctx, Ug = _setup(cs, "fp64")
+    a, b, c = Ug.clone(), Ug.clone(), Ug.clone()
+    na = ctx.rk_smooth(a, 4)              # one graph of 4 iterations
+    nb = ctx.rk_smooth(b, 4)
+    nc = torch.cat([ctx.rk_smooth(c, 1) for _ in range(4)])   # direct launches
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and torch.equal(na, nb)
+    assert torch.equal(a, c) and torch.equal(na, nc)
+
+
+def test_nonfinite_state_is_reported():
+    cs = C.channel(16, 8)
+    o, U, ctx, Ug = _setup(cs, "fp64")
+    flat = ctx.to_compact(Ug)
+    flat[5] = float("nan")
+    ctx.from_compact(flat, Ug)
+    ctx.rk_smooth(Ug, 1)
+    assert ctx.sync_status() == hb.HB_ERR_NONFINITE
+    assert ctx.sync_status() == hb.HB_OK      # the word is cleared after reading
