@@ -203,6 +203,36 @@ hb_status hb_adjoint_residual(hb_ctx* ctx, const void* U, const void* psi, doubl
 hb_status hb_set_timing(hb_ctx* ctx, int enable);
 hb_status hb_kernel_stats(hb_ctx* ctx, int which, double* ms, int64_t* launches, int reset);
 
+/* Limits of hb_residual_norms_noalloc's fixed scratch. */
+#define HB_NOALLOC_MAX_CTAS 2048
+#define HB_NOALLOC_MAX_VARS 8
+#define HB_NOALLOC_MAX_CELLS ((int64_t)1 << 31)
+#define HB_NOALLOC_MAX_VALUES ((int64_t)1 << 40)
+
+/* Allocation-free residual norms, for callers that cannot allocate device
+ * memory (inside a CUDA graph capture, under a pool that forbids growth, or
+ * a host runtime that only hands out pre-registered buffers): no context is
+ * needed and nothing is allocated -- no cudaMalloc/cudaFree, no allocating
+ * library routine.  The paper has no counterpart; it is the norm reduction
+ * of hb_rk_smooth offered without a context.
+ *   norms[v] = sqrt( sum_{n,c} (R[n][v][c] / vol[c])^2 / (ncells * n_snap) )
+ * R: device, [n_snap][nv][ncells] in `prec` (HB_FP32: float, HB_FP64:
+ * double); vol: device, [ncells] in the same type; norms: device FP64 [nv].
+ * Partial sums are FP64 and summed in a fixed order (bitwise reproducible
+ * for a given ncells).  They live in one static device array of
+ * HB_NOALLOC_MAX_CTAS x HB_NOALLOC_MAX_VARS doubles (128 KB) that every GPU
+ * which loads the library holds until the process exits; every call
+ * overwrites the slots it reads, so no clearing is needed, but calls that
+ * overlap on the GPU (different streams, no ordering) race on that array.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Errors: HB_ERR_INVALID_ARG for null pointers, a bad precision or a
+ * non-positive size; HB_ERR_UNSUPPORTED for nv > HB_NOALLOC_MAX_VARS,
+ * ncells > HB_NOALLOC_MAX_CELLS or n_snap*nv*ncells > HB_NOALLOC_MAX_VALUES;
+ * HB_ERR_CUDA if a launch fails.  Asynchronous on `stream`. */
+hb_status hb_residual_norms_noalloc(const void* R, const void* vol, int prec, int64_t ncells,
+                                    int n_snap, int nv, double* norms, void* stream);
+
 /* Synchronise `stream`, then read and clear the device error word. */
 hb_status hb_sync_status(hb_ctx* ctx, void* stream);
 

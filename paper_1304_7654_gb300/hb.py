@@ -98,6 +98,8 @@ def load(path: str | None = None):
     lib.hb_set_timing.argtypes = [_vp, ct.c_int]
     lib.hb_kernel_stats.argtypes = [_vp, ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64),
                                     ct.c_int]
+    lib.hb_residual_norms_noalloc.argtypes = [_vp, _vp, ct.c_int, ct.c_int64, ct.c_int, ct.c_int,
+                                              _vp, _vp]
     lib.hb_last_error.restype = ct.c_char_p
     lib.hb_last_error.argtypes = [_vp]
     _lib = lib
@@ -301,3 +303,15 @@ class HBContext:
 
     def sync_status(self):
         return int(self.lib.hb_sync_status(self.h, _stream()))
+
+
+def residual_norms_noalloc(R, vol, ncells, n_snap, nv, norms):
+    """Binding of hb_residual_norms_noalloc: R [n_snap][nv][ncells] and vol
+    [ncells] (both float32 or both float64 CUDA tensors), norms FP64 [nv]."""
+    import torch
+    prec = HB_FP32 if R.dtype == torch.float32 else HB_FP64
+    st = load().hb_residual_norms_noalloc(_ptr(R), _ptr(vol), prec, int(ncells), int(n_snap), int(nv),
+                                          _ptr(norms), _stream())
+    if st != HB_OK:
+        raise HBError(st, "hb_residual_norms_noalloc")
+    return norms
