@@ -61,6 +61,8 @@ struct hb_ctx {
   void* d_B = nullptr;
   double* d_partials = nullptr; // [ntiles][8]
   double* d_face = nullptr;     // [nwall][ns][3]
+  double* d_coef = nullptr;     // [ns][nbodies][3]
+  unsigned int* d_done = nullptr;
   double* d_ring = nullptr;     // [ring][8] norms ring for graph replays
   int ring = 0;
   int* d_err = nullptr;
@@ -465,6 +467,8 @@ void free_ctx(hb_ctx* c) {
   cudaFree(c->d_B);
   cudaFree(c->d_partials);
   cudaFree(c->d_face);
+  cudaFree(c->d_coef);
+  cudaFree(c->d_done);
   cudaFree(c->d_ring);
   cudaFree(c->d_err);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -626,6 +630,9 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
     CK(cudaMemcpy(ctx->d_walls, Tb.walls.data(), sizeof(BcRec) * ctx->nwall, cudaMemcpyHostToDevice));
     CK(cudaMalloc(&ctx->d_face, sizeof(double) * 3 * ctx->nwall * ctx->ns_max));
   }
+  CK(cudaMalloc(&ctx->d_coef, sizeof(double) * 3 * ctx->ns_max * std::max(1, ctx->n_bodies)));
+  CK(cudaMalloc(&ctx->d_done, sizeof(unsigned int)));
+  CK(cudaMemset(ctx->d_done, 0, sizeof(unsigned int)));
   CK(cudaMalloc(&ctx->d_A, ts * ctx->state_size));
   CK(cudaMalloc(&ctx->d_B, ts * ctx->state_size));
   CK(cudaMemset(ctx->d_A, 0, ts * ctx->state_size));
@@ -799,6 +806,8 @@ hb_status forces_impl(hb_ctx* c, const T* U, double* coef, double* J, cudaStream
   p.coef = coef;
   p.J = J;
   p.nbodies = c->cases[0].d.n_bodies;
+  p.coef_scratch = c->d_coef;
+  p.done = c->d_done;
   if (p.nbodies == 0) {
     if (J) HB_CUDA(c, cudaMemsetAsync(J, 0, sizeof(double), s));
     return HB_OK;

@@ -109,6 +109,8 @@ struct ForceParams {
   double* coef;             // [ns][nbodies][3] or null
   double* J;                // or null
   int nbodies;
+  double* coef_scratch;     // [ns][nbodies][3] library-owned
+  unsigned int* done;       // completion counter (zero between launches)
 };
 
 // launchers (defined per precision in hb_kernels_f32.cu / hb_kernels_f64.cu)

@@ -61,46 +61,71 @@ __device__ __forceinline__ void rotp(const Fr<T>& f, T x, T y, T& ox, T& oy) {
   oy = f.s * rx + f.c * ry + f.py;
 }
 
+// Precision-specific arithmetic.  The FP32 path uses the hardware reciprocal
+// and reciprocal-square-root forms (a few ulp each, well inside the FP32
+// error budget of the residual); the FP64 path keeps correctly rounded
+// division and square root.
+template <typename T>
+struct Ar;
+template <>
+struct Ar<float> {
+  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ float rcp(float b) { return __fdividef(1.0f, b); }
+  static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+};
+template <>
+struct Ar<double> {
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double rcp(double b) { return 1.0 / b; }
+  static __device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
+};
+
 template <typename T>
 __device__ __forceinline__ T van_albada(T a, T b, T eps) {
-  return ((b * b + eps) * a + (a * a + eps) * b) / (a * a + b * b + T(2) * eps);
+  return Ar<T>::div((b * b + eps) * a + (a * a + eps) * b, a * a + b * b + T(2) * eps);
 }
 
 // Roe flux through area vector (Sx, Sy) of a face moving with normal speed
 // vgn (grid velocity . unit normal).  W = (rho, u, v, p).  F = (mass, mx, my, E).
+// gg1 = gamma/(gamma-1), ig1 = 1/(gamma-1).
 template <typename T>
-__device__ __forceinline__ void roe2d(const T* WL, const T* WR, T Sx, T Sy, T vgn, T gam,
-                                      int efix, T efrac, T* F) {
-  const T A = sqrt(Sx * Sx + Sy * Sy);
-  const T nx = Sx / A, ny = Sy / A;
-  const T gm1 = gam - T(1);
+__device__ __forceinline__ void roe2d(const T* WL, const T* WR, T Sx, T Sy, T vgn, T gm1, T gg1,
+                                      T ig1, int efix, T efrac, T* F) {
+  const T A2 = Sx * Sx + Sy * Sy;
+  const T iA = Ar<T>::rsq(A2);
+  const T A = A2 * iA;
+  const T nx = Sx * iA, ny = Sy * iA;
+  const T irL = Ar<T>::rcp(WL[0]), irR = Ar<T>::rcp(WR[0]);
   const T qL = WL[1] * nx + WL[2] * ny;
   const T qR = WR[1] * nx + WR[2] * ny;
   const T kL = T(0.5) * (WL[1] * WL[1] + WL[2] * WL[2]);
   const T kR = T(0.5) * (WR[1] * WR[1] + WR[2] * WR[2]);
-  const T HL = gam / gm1 * WL[3] / WL[0] + kL;
-  const T HR = gam / gm1 * WR[3] / WR[0] + kR;
-  const T r = sqrt(WR[0] / WL[0]);
+  const T HL = gg1 * WL[3] * irL + kL;
+  const T HR = gg1 * WR[3] * irR + kR;
+  const T rr = WR[0] * irL;
+  const T r = rr * Ar<T>::rsq(rr);          // sqrt(rho_R / rho_L)
   const T rt = r * WL[0];
-  const T inv1r = T(1) / (T(1) + r);
+  const T inv1r = Ar<T>::rcp(T(1) + r);
   const T ut = (WL[1] + r * WR[1]) * inv1r;
   const T vt = (WL[2] + r * WR[2]) * inv1r;
   const T Ht = (HL + r * HR) * inv1r;
   const T kt = T(0.5) * (ut * ut + vt * vt);
   const T ct2 = gm1 * (Ht - kt);
-  const T ct = sqrt(ct2);
+  const T ict = Ar<T>::rsq(ct2);
+  const T ct = ct2 * ict;
+  const T ict2 = ict * ict;
   const T qt = ut * nx + vt * ny;
   const T qtr = qt - vgn;
   T l1 = fabs(qtr - ct), l2 = fabs(qtr), l3 = fabs(qtr + ct);
   if (efix) {
     const T del = efrac * ct;
-    if (l1 < del) l1 = (l1 * l1 + del * del) / (T(2) * del);
-    if (l3 < del) l3 = (l3 * l3 + del * del) / (T(2) * del);
+    if (l1 < del) l1 = (l1 * l1 + del * del) * (T(0.5) * Ar<T>::rcp(del));
+    if (l3 < del) l3 = (l3 * l3 + del * del) * (T(0.5) * Ar<T>::rcp(del));
   }
   const T dp = WR[3] - WL[3], drho = WR[0] - WL[0], dq = qR - qL;
-  const T a1 = (dp - rt * ct * dq) / (T(2) * ct2);
-  const T a3 = (dp + rt * ct * dq) / (T(2) * ct2);
-  const T a2 = drho - dp / ct2;
+  const T a1 = T(0.5) * (dp - rt * ct * dq) * ict2;
+  const T a3 = T(0.5) * (dp + rt * ct * dq) * ict2;
+  const T a2 = drho - dp * ict2;
   const T dux = (WR[1] - WL[1]) - dq * nx;
   const T duy = (WR[2] - WL[2]) - dq * ny;
   const T udu = ut * dux + vt * duy;
@@ -110,7 +135,7 @@ __device__ __forceinline__ void roe2d(const T* WL, const T* WR, T Sx, T Sy, T vg
   const T D2 = w1 * (vt - ct * ny) + l2 * (a2 * vt + rt * duy) + w3 * (vt + ct * ny);
   const T D3 = w1 * (Ht - ct * qt) + l2 * (a2 * kt + rt * udu) + w3 * (Ht + ct * qt);
   const T qLr = qL - vgn, qRr = qR - vgn;
-  const T EL = WL[3] / gm1 + WL[0] * kL, ER = WR[3] / gm1 + WR[0] * kR;
+  const T EL = WL[3] * ig1 + WL[0] * kL, ER = WR[3] * ig1 + WR[0] * kR;
   const T hA = T(0.5) * A;
   F[0] = hA * (WL[0] * qLr + WR[0] * qRr - D0);
   F[1] = hA * (WL[0] * WL[1] * qLr + WL[3] * nx + WR[0] * WR[1] * qRr + WR[3] * nx - D1);
@@ -123,15 +148,15 @@ __device__ __forceinline__ void roe2d(const T* WL, const T* WR, T Sx, T Sy, T vg
 template <typename T>
 __device__ __forceinline__ void visc2d(const T* gL, const T* gR, T uL, T vL, T TL, T uR, T vR,
                                        T TR, T tx, T ty, T Sx, T Sy, T mu, T kap, T* Fv) {
-  const T len = sqrt(tx * tx + ty * ty);
-  const T ex = tx / len, ey = ty / len;
+  const T il = Ar<T>::rsq(tx * tx + ty * ty);
+  const T ex = tx * il, ey = ty * il;
   T g[6];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     const T bx = T(0.5) * (gL[2 * q] + gR[2 * q]);
     const T by = T(0.5) * (gL[2 * q + 1] + gR[2 * q + 1]);
     const T dphi = (q == 0) ? (uR - uL) : (q == 1) ? (vR - vL) : (TR - TL);
-    const T corr = dphi / len - (bx * ex + by * ey);
+    const T corr = dphi * il - (bx * ex + by * ey);
     g[2 * q] = bx + corr * ex;
     g[2 * q + 1] = by + corr * ey;
   }
@@ -148,10 +173,10 @@ __device__ __forceinline__ void visc2d(const T* gL, const T* gR, T uL, T vL, T T
   Fv[3] = uf * fx + vf * fy + kap * (g[4] * Sx + g[5] * Sy);
 }
 
-template <typename T>
-__host__ __device__ constexpr size_t tile2d_smem_elems(int TI, int TJ) {
-  return (size_t)17 * (TI + 4) * (TJ + 4) + (size_t)6 * (TI + 2) * (TJ + 2) +
-         (size_t)4 * ((TI + 1) * TJ + TI * (TJ + 1));
+// shared-memory elements of one tile CTA
+__host__ __device__ constexpr size_t tile2d_smem_elems(int TI, int TJ, int NS) {
+  return (size_t)18 * (TI + 4) * (TJ + 4) + (size_t)6 * (TI + 2) * (TJ + 2) +
+         (size_t)4 * ((TI + 1) * TJ + TI * (TJ + 1)) + (size_t)NS * 4 * TI * TJ + (size_t)NS * NS;
 }
 
 // block-wide FP64 sum of up to 8 values, fixed order; result valid in thread 0
@@ -180,7 +205,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   const int4 tl = P.tiles[t];
   const BlockDev B = P.blocks[tl.x];
   const CaseDev<T>* C = P.cases + B.cs;
-  const int TI = P.TI, TJ = P.TJ;
+  const int TI = P.TI, TJ = P.TJ, NT = TI * TJ;
   const int RI = TI + 4, RJ = TJ + 4, NR = RI * RJ;
   const int GI = TI + 2, NG = GI * (TJ + 2);
   const int NFI = (TI + 1) * TJ, NF = NFI + TI * (TJ + 1);
@@ -190,67 +215,68 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   const int n0 = B.n[0], n1 = B.n[1];
 
   T* sW = sm;              // [4][NR] primitives rho, u, v, p
-  T* sVol = sW + 4 * NR;   // [NR]
-  T* sDc = sVol + NR;      // [d*2+comp][NR] centre minus low-neighbour centre
-  T* sS = sDc + 4 * NR;    // [d*2+comp][NR]
-  T* sXf = sS + 4 * NR;    // [d*2+comp][NR]
-  T* sG = sXf + 4 * NR;    // [6][NG]
-  T* sF = sG + 6 * NG;     // [NV][NF]
+  T* sT = sW + 4 * NR;     // [NR] temperature gamma p / rho
+  T* sIV = sT + NR;        // [NR] 1 / volume
+  T* sS = sIV + NR;        // [d*2+comp][NR] low-face vectors
+  T* sDc = sS + 4 * NR;    // [d*2+comp][NR] centre minus low-neighbour centre
+  T* sXf = sDc + 4 * NR;   // [d*2+comp][NR] low-face centroids (moving grids)
+  T* sG = sXf + 4 * NR;    // [6][NG] gradients on the 1-cell ring
+  T* sF = sG + 6 * NG;     // [NV][NF] face fluxes
+  T* sAcc = sF + 4 * NF;   // [NS][NV][NT] flux balance per snapshot of each own cell
+  T* sD = sAcc + NS * NV * NT;   // [NS][NS]
 
   const T gam = C->gamma, gm1 = C->gamma - T(1), eps = C->eps, efrac = C->ent_frac;
+  const T gg1 = gam / gm1, ig1 = T(1) / gm1;
   const T mu = C->mu, kap = C->kappa, omega = C->omega;
   const int efix = C->entropy_fix;
   const bool moving = C->motion != 0;
 
-  // ---- static geometry of the region (tile + 2-cell halo)
+  // ---- static geometry of the region (tile + 2-cell halo), once per stage
   for (int r = tid; r < NR; r += nt) {
     const int ri = r % RI, rj = r / RI;
     const int i = i0 - 2 + ri, j = j0 - 2 + rj;
     if (i <= n0 + 1 && j <= n1 + 1) {
       const int64_t c = B.goff + (int64_t)(j + 2) * P0 + (i + 2);
-      sVol[r] = P.g.q[G_VOL][c];
-      sDc[r] = P.g.q[G_DC + 0][c];
-      sDc[NR + r] = P.g.q[G_DC + 1][c];
-      sDc[2 * NR + r] = P.g.q[G_DC + 3][c];
-      sDc[3 * NR + r] = P.g.q[G_DC + 4][c];
+      sIV[r] = Ar<T>::rcp(P.g.q[G_VOL][c]);
       sS[r] = P.g.q[G_S + 0][c];
       sS[NR + r] = P.g.q[G_S + 1][c];
       sS[2 * NR + r] = P.g.q[G_S + 3][c];
       sS[3 * NR + r] = P.g.q[G_S + 4][c];
+      if (VISC) {
+        sDc[r] = P.g.q[G_DC + 0][c];
+        sDc[NR + r] = P.g.q[G_DC + 1][c];
+        sDc[2 * NR + r] = P.g.q[G_DC + 3][c];
+        sDc[3 * NR + r] = P.g.q[G_DC + 4][c];
+      }
       if (moving) {
         sXf[r] = P.g.q[G_XF + 0][c];
         sXf[NR + r] = P.g.q[G_XF + 1][c];
         sXf[2 * NR + r] = P.g.q[G_XF + 3][c];
         sXf[3 * NR + r] = P.g.q[G_XF + 4][c];
       }
-    } else {   // outside the padded block: benign unit cell, never used by own cells
-      sVol[r] = T(1);
-      sDc[r] = T(1);
-      sDc[NR + r] = T(0);
-      sDc[2 * NR + r] = T(0);
-      sDc[3 * NR + r] = T(1);
+    } else {   // outside the padded block: a benign unit cell, never used by own cells
+      sIV[r] = T(1);
       sS[r] = T(1);
       sS[NR + r] = T(0);
       sS[2 * NR + r] = T(0);
       sS[3 * NR + r] = T(1);
+      sDc[r] = T(1);
+      sDc[NR + r] = T(0);
+      sDc[2 * NR + r] = T(0);
+      sDc[3 * NR + r] = T(1);
       sXf[r] = T(0);
       sXf[NR + r] = T(0);
       sXf[2 * NR + r] = T(0);
       sXf[3 * NR + r] = T(0);
     }
   }
+  for (int e = tid; e < NS * NS; e += nt) sD[e] = C->D[e];
 
   const int ti = tid & (TI - 1), tj = tid >> P.ti_shift;
   const int ci = i0 + ti, cj = j0 + tj;
-  const bool own = (tid < TI * TJ) && ci < n0 && cj < n1;
+  const bool own = (tid < NT) && ci < n0 && cj < n1;
   const int rown = (tj + 2) * RI + (ti + 2);
   const int64_t cown = (int64_t)(cj + 2) * P0 + (ci + 2);
-
-  T acc[NS][NV], h[NS][NV];
-#pragma unroll
-  for (int m = 0; m < NS; ++m)
-#pragma unroll
-    for (int v = 0; v < NV; ++v) { acc[m][v] = T(0); h[m][v] = T(0); }
 
   for (int n = 0; n < NS; ++n) {
     const Fr<T> f = frame_at(C, n);
@@ -259,49 +285,50 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
     for (int r = tid; r < NR; r += nt) {
       const int ri = r % RI, rj = r / RI;
       const int i = i0 - 2 + ri, j = j0 - 2 + rj;
-      T w0 = T(1), w1 = T(0), w2 = T(0), w3 = T(1);
+      T w0 = T(1), w1 = T(0), w2 = T(0), w3 = T(1), tt = gam;
       if (i <= n0 + 1 && j <= n1 + 1) {
         const T* u = P.Uprev + B.off + (int64_t)n * NV * B.plane + (int64_t)(j + 2) * P0 + (i + 2);
         const T rho = u[0], mx = u[B.plane], my = u[2 * B.plane], E = u[3 * B.plane];
+        const T ir = Ar<T>::rcp(rho);
         w0 = rho;
-        w1 = mx / rho;
-        w2 = my / rho;
+        w1 = mx * ir;
+        w2 = my * ir;
         w3 = gm1 * (E - T(0.5) * rho * (w1 * w1 + w2 * w2));
+        tt = gam * w3 * ir;
       }
       sW[r] = w0;
       sW[NR + r] = w1;
       sW[2 * NR + r] = w2;
       sW[3 * NR + r] = w3;
+      sT[r] = tt;
     }
     __syncthreads();
-    // ---- Green-Gauss gradients of (u, v, T) on the 1-cell ring
+    // ---- Green-Gauss gradients of (u, v, T) on the 1-cell ring, written as
+    // sum (phi_nb - phi_c)/2 S over the closed cell (the faces sum to zero),
+    // which keeps the rounding of large face vectors out of small cells
     if (VISC) {
       for (int gq = tid; gq < NG; gq += nt) {
         const int gi = gq % GI, gj = gq / GI;
         const int r = (gj + 1) * RI + (gi + 1);
-        // Green-Gauss with face values (phi_c + phi_nb)/2 over a closed cell,
-        // written as sum (phi_nb - phi_c)/2 S (the faces sum to zero), which
-        // keeps the rounding of large face vectors out of small cells
-        const T uc = sW[NR + r], vc = sW[2 * NR + r], Tc = gam * sW[3 * NR + r] / sW[r];
+        const T uc = sW[NR + r], vc = sW[2 * NR + r], Tc = sT[r];
         T g[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
         const int nb[4] = {r - 1, r + 1, r - RI, r + RI};
         const int fo[4] = {r, r + 1, r, r + RI};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int d = k >> 1;
-          const T sg = (k & 1) ? T(1) : T(-1);
+          const T sg = (k & 1) ? T(0.5) : T(-0.5);
           T sx, sy;
           rotv(f, sS[(2 * d) * NR + fo[k]], sS[(2 * d + 1) * NR + fo[k]], sx, sy);
           sx *= sg;
           sy *= sg;
           const int o = nb[k];
-          const T un = sW[NR + o], vn = sW[2 * NR + o], Tn = gam * sW[3 * NR + o] / sW[o];
-          const T fu = T(0.5) * (un - uc), fv = T(0.5) * (vn - vc), fT = T(0.5) * (Tn - Tc);
-          g[0] += fu * sx; g[1] += fu * sy;
-          g[2] += fv * sx; g[3] += fv * sy;
-          g[4] += fT * sx; g[5] += fT * sy;
+          const T du = sW[NR + o] - uc, dv = sW[2 * NR + o] - vc, dT = sT[o] - Tc;
+          g[0] += du * sx; g[1] += du * sy;
+          g[2] += dv * sx; g[3] += dv * sy;
+          g[4] += dT * sx; g[5] += dT * sy;
         }
-        const T iv = T(1) / sVol[r];
+        const T iv = sIV[r];
 #pragma unroll
         for (int q = 0; q < 6; ++q) sG[q * NG + gq] = g[q] * iv;
       }
@@ -342,20 +369,19 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
         T xf, yf;
         rotp(f, sXf[(2 * d) * NR + rR], sXf[(2 * d + 1) * NR + rR], xf, yf);
         const T vgx = -f.thd * (yf - f.py), vgy = f.thd * (xf - f.px);
-        vgn = (vgx * sx + vgy * sy) / sqrt(sx * sx + sy * sy);
+        vgn = (vgx * sx + vgy * sy) * Ar<T>::rsq(sx * sx + sy * sy);
       }
       T F[4];
-      roe2d(WL, WR, sx, sy, vgn, gam, efix, efrac, F);
+      roe2d(WL, WR, sx, sy, vgn, gm1, gg1, ig1, efix, efrac, F);
       if (VISC) {
         T gl[6], gr[6];
 #pragma unroll
         for (int q = 0; q < 6; ++q) { gl[q] = sG[q * NG + gLi]; gr[q] = sG[q * NG + gRi]; }
         T tx, ty;
         rotv(f, sDc[(2 * d) * NR + rR], sDc[(2 * d + 1) * NR + rR], tx, ty);
-        const T TL = gam * sW[3 * NR + rL] / sW[rL], TR = gam * sW[3 * NR + rR] / sW[rR];
         T Fv[4];
-        visc2d(gl, gr, sW[NR + rL], sW[2 * NR + rL], TL, sW[NR + rR], sW[2 * NR + rR], TR, tx, ty,
-               sx, sy, mu, kap, Fv);
+        visc2d(gl, gr, sW[NR + rL], sW[2 * NR + rL], sT[rL], sW[NR + rR], sW[2 * NR + rR], sT[rR], tx,
+               ty, sx, sy, mu, kap, Fv);
 #pragma unroll
         for (int q = 0; q < 4; ++q) F[q] -= Fv[q];
       }
@@ -366,43 +392,44 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
     if (own) {
       const int fi0 = tj * (TI + 1) + ti;
       const int fj0 = NFI + tj * TI + ti;
-      T Rn[NV];
 #pragma unroll
       for (int q = 0; q < NV; ++q)
-        Rn[q] = (sF[q * NF + fi0 + 1] - sF[q * NF + fi0]) + (sF[q * NF + fj0 + TI] - sF[q * NF + fj0]);
-#pragma unroll
-      for (int m = 0; m < NS - 1; ++m)
-#pragma unroll
-        for (int q = 0; q < NV; ++q) acc[m][q] = acc[m + 1][q];
-#pragma unroll
-      for (int q = 0; q < NV; ++q) acc[NS - 1][q] = Rn[q];
-      const T* u = P.Uprev + B.off + (int64_t)n * NV * B.plane + cown;
-      T uc[NV];
-#pragma unroll
-      for (int q = 0; q < NV; ++q) uc[q] = u[q * B.plane];
-#pragma unroll
-      for (int m = 0; m < NS; ++m) {
-        const T dmn = C->D[m * NS + n];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) h[m][q] += dmn * uc[q];
-      }
+        sAcc[(n * NV + q) * NT + tid] =
+            (sF[q * NF + fi0 + 1] - sF[q * NF + fi0]) + (sF[q * NF + fj0 + TI] - sF[q * NF + fj0]);
     }
   }
 
   // ---- epilogue: HB source, residual or RK update, norm partials
-  // norm partials: squares summed over this cell's snapshots in T, then
-  // accumulated across cells and CTAs in FP64
   T tacc[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) tacc[q] = T(0);
   double nacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (own) {
-    const T V = sVol[rown];
+    const T V = P.g.q[G_VOL][B.goff + cown];
     const T vw = V * omega;
+    const T iV = sIV[rown];
+    // the own cell at every snapshot (recently staged, served from cache)
+    T uu[NS][NV];
+#pragma unroll
+    for (int m = 0; m < NS; ++m)
+#pragma unroll
+      for (int q = 0; q < NV; ++q)
+        uu[m][q] = P.Uprev[B.off + ((int64_t)m * NV + q) * B.plane + cown];
+    // mean face vectors of the own cell (static frame)
+    const T a0x = T(0.5) * (sS[rown] + sS[rown + 1]), a0y = T(0.5) * (sS[NR + rown] + sS[NR + rown + 1]);
+    const T b0x = T(0.5) * (sS[2 * NR + rown] + sS[2 * NR + rown + RI]);
+    const T b0y = T(0.5) * (sS[3 * NR + rown] + sS[3 * NR + rown + RI]);
+    const T ma2 = a0x * a0x + a0y * a0y, mb2 = b0x * b0x + b0y * b0y;
+    const T ma = ma2 * Ar<T>::rsq(ma2), mb = mb2 * Ar<T>::rsq(mb2);
     for (int n = 0; n < NS; ++n) {
       T Rn[NV];
 #pragma unroll
-      for (int q = 0; q < NV; ++q) Rn[q] = acc[0][q] + vw * h[0][q];
+      for (int q = 0; q < NV; ++q) {
+        T h = T(0);
+#pragma unroll
+        for (int m = 0; m < NS; ++m) h += sD[n * NS + m] * uu[m][q];
+        Rn[q] = sAcc[(n * NV + q) * NT + tid] + vw * h;
+      }
       const int64_t base = B.off + (int64_t)n * NV * B.plane + cown;
       if (MODE == 0) {
 #pragma unroll
@@ -412,10 +439,12 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
 #pragma unroll
         for (int q = 0; q < NV; ++q) u0[q] = P.U0[base + q * B.plane];
         const Fr<T> f = frame_at(C, n);
-        const T rho = u0[0], uu = u0[1] / rho, vv = u0[2] / rho;
-        const T pp = gm1 * (u0[3] - T(0.5) * rho * (uu * uu + vv * vv));
-        const T cs = sqrt(gam * pp / rho);
-        T urx = uu, ury = vv;
+        const T rho = u0[0], irho = Ar<T>::rcp(rho);
+        const T uv = u0[1] * irho, vv = u0[2] * irho;
+        const T pp = gm1 * (u0[3] - T(0.5) * rho * (uv * uv + vv * vv));
+        const T c2 = gam * pp * irho;
+        const T cs = c2 * Ar<T>::rsq(c2);
+        T urx = uv, ury = vv;
         if (moving) {
           T xc, yc;
           rotp(f, P.g.q[G_XC][B.goff + cown], P.g.q[G_XC + 1][B.goff + cown], xc, yc);
@@ -423,22 +452,19 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
           ury -= f.thd * (xc - f.px);
         }
         T ax, ay, bx, by;
-        rotv(f, T(0.5) * (sS[rown] + sS[rown + 1]), T(0.5) * (sS[NR + rown] + sS[NR + rown + 1]), ax, ay);
-        rotv(f, T(0.5) * (sS[2 * NR + rown] + sS[2 * NR + rown + RI]),
-             T(0.5) * (sS[3 * NR + rown] + sS[3 * NR + rown + RI]), bx, by);
-        const T ma2 = ax * ax + ay * ay, mb2 = bx * bx + by * by;
-        T lam = fabs(urx * ax + ury * ay) + cs * sqrt(ma2) + fabs(urx * bx + ury * by) + cs * sqrt(mb2);
+        rotv(f, a0x, a0y, ax, ay);
+        rotv(f, b0x, b0y, bx, by);
+        T lam = fabs(urx * ax + ury * ay) + cs * ma + fabs(urx * bx + ury * by) + cs * mb;
         if (VISC) {
           const T cv = (gam / C->prandtl > T(4.0 / 3.0)) ? gam / C->prandtl : T(4.0 / 3.0);
-          lam += T(4) * cv * (mu / rho) * (ma2 + mb2) / V;
+          lam += T(4) * cv * (mu * irho) * (ma2 + mb2) * iV;
         }
         lam += omega * T(C->nh) * V;
-        const T dtau = C->cfl * V / lam;
-        const T fac = P.alpha * dtau / V;
+        // dtau / V = cfl / lambda
+        const T fac = P.alpha * C->cfl * Ar<T>::rcp(lam);
 #pragma unroll
         for (int q = 0; q < NV; ++q) P.Unext[base + q * B.plane] = u0[q] - fac * Rn[q];
         if (P.partials) {
-          const T iV = T(1) / V;
 #pragma unroll
           for (int q = 0; q < NV; ++q) {
             const T x = Rn[q] * iV;
@@ -446,10 +472,6 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
           }
         }
       }
-#pragma unroll
-      for (int m = 0; m < NS - 1; ++m)
-#pragma unroll
-        for (int q = 0; q < NV; ++q) { acc[m][q] = acc[m + 1][q]; h[m][q] = h[m + 1][q]; }
     }
   }
 #pragma unroll
@@ -464,7 +486,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
 }
 
 template <typename T, int NS, bool VISC, int MODE>
-__global__ void __launch_bounds__(MAXNT) tile2d_kernel(StageParams<T> P) {
+__global__ void __launch_bounds__(MAXNT, (sizeof(T) == 4) ? 2 : 1) tile2d_kernel(StageParams<T> P) {
   extern __shared__ __align__(16) unsigned char smraw[];
   tile2d<T, NS, VISC, MODE>(P, blockIdx.x, reinterpret_cast<T*>(smraw));
 }
@@ -700,25 +722,44 @@ __global__ void force_faces_kernel(ForceParams<T> p) {
              : 0.0;
 }
 
-// fixed-order FP64 sums per (snapshot, body, component), then J
+// fixed-order FP64 sums per (snapshot, body): CTA (n, b) strides over the
+// wall faces, then a fixed warp/tree order; the last CTA to finish forms J
 template <typename T>
-__global__ void force_finish_kernel(ForceParams<T> p) {
-  extern __shared__ double fsm[];
-  const int tot = p.ns * p.nbodies * 3;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int k = e % 3, b = (e / 3) % p.nbodies, n = e / (3 * p.nbodies);
-    double s = 0.0;
-    for (int rec = 0; rec < p.nwall; ++rec)
-      if (p.walls[rec].body == b) s += p.face_out[((int64_t)rec * p.ns + n) * 3 + k];
-    fsm[e] = s;
-    if (p.coef) p.coef[e] = s;
+__global__ void force_finish_kernel(ForceParams<T> p, unsigned int* done) {
+  __shared__ double red[32][3];
+  const int n = blockIdx.x / p.nbodies, b = blockIdx.x % p.nbodies;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int rec = threadIdx.x; rec < p.nwall; rec += blockDim.x)
+    if (p.walls[rec].body == b)
+      for (int k = 0; k < 3; ++k) acc[k] += p.face_out[((int64_t)rec * p.ns + n) * 3 + k];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < 3; ++k) {
+    double x = acc[k];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) red[warp][k] = x;
   }
   __syncthreads();
-  if (threadIdx.x == 0 && p.J) {
-    double j = 0.0;
-    for (int n = 0; n < p.ns; ++n)
-      for (int b = 0; b < p.nbodies; ++b) j += fsm[(n * p.nbodies + b) * 3];
-    *p.J = j / (double)p.ns;
+  if (threadIdx.x < 3) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w][threadIdx.x];
+    p.coef_scratch[(n * p.nbodies + b) * 3 + threadIdx.x] = sum;
+    if (p.coef) p.coef[(n * p.nbodies + b) * 3 + threadIdx.x] = sum;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int ticket = atomicAdd(done, 1u);
+    if (ticket == gridDim.x - 1) {      // last CTA: every partial is visible
+      __threadfence();
+      if (p.J) {
+        double j = 0.0;
+        for (int nn = 0; nn < p.ns; ++nn)
+          for (int bb = 0; bb < p.nbodies; ++bb)
+            j += ((volatile double*)p.coef_scratch)[(nn * p.nbodies + bb) * 3];
+        *p.J = j / (double)p.ns;
+      }
+      *done = 0u;                       // ready for the next launch
+    }
   }
 }
 
