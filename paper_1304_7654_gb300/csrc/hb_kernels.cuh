@@ -175,7 +175,7 @@ __device__ __forceinline__ void visc2d(const T* gL, const T* gR, T uL, T vL, T T
 
 // shared-memory elements of one tile CTA
 __host__ __device__ constexpr size_t tile2d_smem_elems(int TI, int TJ, int NS) {
-  return (size_t)18 * (TI + 4) * (TJ + 4) + (size_t)6 * (TI + 2) * (TJ + 2) +
+  return (size_t)10 * (TI + 4) * (TJ + 4) + (size_t)6 * (TI + 2) * (TJ + 2) +
          (size_t)4 * ((TI + 1) * TJ + TI * (TJ + 1)) + (size_t)NS * 4 * TI * TJ + (size_t)NS * NS;
 }
 
@@ -199,16 +199,19 @@ __device__ __forceinline__ void block_sum8(double* v, int nv, double* scratch) {
 }
 
 // MODE 0: R := residual.  MODE 1: RK stage update (+ norm partials if set).
-template <typename T, int NS, bool VISC, int MODE>
+// The tile shape TI x TJ (TI a power of two) is a compile-time constant so that
+// every flat-index decomposition is a multiply-shift.
+template <typename T, int NS, bool VISC, int MODE, int TI, int TJ>
 __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   constexpr int NV = 4;
   const int4 tl = P.tiles[t];
   const BlockDev B = P.blocks[tl.x];
   const CaseDev<T>* C = P.cases + B.cs;
-  const int TI = P.TI, TJ = P.TJ, NT = TI * TJ;
-  const int RI = TI + 4, RJ = TJ + 4, NR = RI * RJ;
-  const int GI = TI + 2, NG = GI * (TJ + 2);
-  const int NFI = (TI + 1) * TJ, NF = NFI + TI * (TJ + 1);
+  constexpr int NT = TI * TJ;
+  constexpr int RI = TI + 4, RJ = TJ + 4, NR = RI * RJ;
+  constexpr int GI = TI + 2, NG = GI * (TJ + 2);
+  constexpr int NFI = (TI + 1) * TJ, NF = NFI + TI * (TJ + 1);
+  static_assert((TI & (TI - 1)) == 0 && NT <= MAXNT, "tile shape");
   const int i0 = tl.y, j0 = tl.z;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int P0 = B.P[0];
@@ -218,9 +221,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   T* sT = sW + 4 * NR;     // [NR] temperature gamma p / rho
   T* sIV = sT + NR;        // [NR] 1 / volume
   T* sS = sIV + NR;        // [d*2+comp][NR] low-face vectors
-  T* sDc = sS + 4 * NR;    // [d*2+comp][NR] centre minus low-neighbour centre
-  T* sXf = sDc + 4 * NR;   // [d*2+comp][NR] low-face centroids (moving grids)
-  T* sG = sXf + 4 * NR;    // [6][NG] gradients on the 1-cell ring
+  T* sG = sS + 4 * NR;     // [6][NG] gradients on the 1-cell ring
   T* sF = sG + 6 * NG;     // [NV][NF] face fluxes
   T* sAcc = sF + 4 * NF;   // [NS][NV][NT] flux balance per snapshot of each own cell
   T* sD = sAcc + NS * NV * NT;   // [NS][NS]
@@ -242,37 +243,17 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
       sS[NR + r] = P.g.q[G_S + 1][c];
       sS[2 * NR + r] = P.g.q[G_S + 3][c];
       sS[3 * NR + r] = P.g.q[G_S + 4][c];
-      if (VISC) {
-        sDc[r] = P.g.q[G_DC + 0][c];
-        sDc[NR + r] = P.g.q[G_DC + 1][c];
-        sDc[2 * NR + r] = P.g.q[G_DC + 3][c];
-        sDc[3 * NR + r] = P.g.q[G_DC + 4][c];
-      }
-      if (moving) {
-        sXf[r] = P.g.q[G_XF + 0][c];
-        sXf[NR + r] = P.g.q[G_XF + 1][c];
-        sXf[2 * NR + r] = P.g.q[G_XF + 3][c];
-        sXf[3 * NR + r] = P.g.q[G_XF + 4][c];
-      }
     } else {   // outside the padded block: a benign unit cell, never used by own cells
       sIV[r] = T(1);
       sS[r] = T(1);
       sS[NR + r] = T(0);
       sS[2 * NR + r] = T(0);
       sS[3 * NR + r] = T(1);
-      sDc[r] = T(1);
-      sDc[NR + r] = T(0);
-      sDc[2 * NR + r] = T(0);
-      sDc[3 * NR + r] = T(1);
-      sXf[r] = T(0);
-      sXf[NR + r] = T(0);
-      sXf[2 * NR + r] = T(0);
-      sXf[3 * NR + r] = T(0);
     }
   }
   for (int e = tid; e < NS * NS; e += nt) sD[e] = C->D[e];
 
-  const int ti = tid & (TI - 1), tj = tid >> P.ti_shift;
+  const int ti = tid % TI, tj = tid / TI;
   const int ci = i0 + ti, cj = j0 + tj;
   const bool own = (tid < NT) && ci < n0 && cj < n1;
   const int rown = (tj + 2) * RI + (ti + 2);
@@ -334,11 +315,13 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
       }
       __syncthreads();
     }
-    // ---- every face of the tile once
+    // ---- every face of the tile once (faces no own cell uses are skipped)
     for (int fq = tid; fq < NF; fq += nt) {
-      int rL, st, d, gLi, gRi;
+      int rL, st, d, gLi, gRi, fi, fj;
       if (fq < NFI) {
-        const int fi = fq % (TI + 1), fj = fq / (TI + 1);
+        fi = fq % (TI + 1);
+        fj = fq / (TI + 1);
+        if (i0 + fi > n0 || j0 + fj >= n1) continue;
         rL = (fj + 2) * RI + (fi + 1);
         st = 1;
         d = 0;
@@ -346,7 +329,9 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
         gRi = gLi + 1;
       } else {
         const int g2 = fq - NFI;
-        const int fi = g2 % TI, fj = g2 / TI;
+        fi = g2 % TI;
+        fj = g2 / TI;
+        if (i0 + fi >= n0 || j0 + fj > n1) continue;
         rL = (fj + 1) * RI + (fi + 2);
         st = RI;
         d = 1;
@@ -354,6 +339,8 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
         gRi = gLi + GI;
       }
       const int rR = rL + st;
+      // the face is the low face of cell R = (i0 + fi, j0 + fj) along d
+      const int64_t gR = B.goff + (int64_t)(j0 + fj + 2) * P0 + (i0 + fi + 2);
       T WL[4], WR[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -367,7 +354,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
       T vgn = T(0);
       if (moving) {
         T xf, yf;
-        rotp(f, sXf[(2 * d) * NR + rR], sXf[(2 * d + 1) * NR + rR], xf, yf);
+        rotp(f, __ldg(P.g.q[G_XF + 3 * d] + gR), __ldg(P.g.q[G_XF + 3 * d + 1] + gR), xf, yf);
         const T vgx = -f.thd * (yf - f.py), vgy = f.thd * (xf - f.px);
         vgn = (vgx * sx + vgy * sy) * Ar<T>::rsq(sx * sx + sy * sy);
       }
@@ -378,7 +365,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
 #pragma unroll
         for (int q = 0; q < 6; ++q) { gl[q] = sG[q * NG + gLi]; gr[q] = sG[q * NG + gRi]; }
         T tx, ty;
-        rotv(f, sDc[(2 * d) * NR + rR], sDc[(2 * d + 1) * NR + rR], tx, ty);
+        rotv(f, __ldg(P.g.q[G_DC + 3 * d] + gR), __ldg(P.g.q[G_DC + 3 * d + 1] + gR), tx, ty);
         T Fv[4];
         visc2d(gl, gr, sW[NR + rL], sW[2 * NR + rL], sT[rL], sW[NR + rR], sW[2 * NR + rR], sT[rR], tx,
                ty, sx, sy, mu, kap, Fv);
@@ -485,11 +472,17 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   }
 }
 
-template <typename T, int NS, bool VISC, int MODE>
-__global__ void __launch_bounds__(MAXNT, (sizeof(T) == 4) ? 2 : 1) tile2d_kernel(StageParams<T> P) {
+template <typename T, int NS, bool VISC, int MODE, int TI, int TJ>
+__global__ void __launch_bounds__(TI * TJ, (sizeof(T) == 4 ? 3 : 1) * (MAXNT / (TI * TJ)))
+    tile2d_kernel(StageParams<T> P) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  tile2d<T, NS, VISC, MODE>(P, blockIdx.x, reinterpret_cast<T*>(smraw));
+  tile2d<T, NS, VISC, MODE, TI, TJ>(P, blockIdx.x, reinterpret_cast<T*>(smraw));
 }
+
+// tile shapes built into the library (index = StageParams shape id)
+constexpr int kTileShapes = 3;
+__host__ __device__ constexpr int tile_ti(int id) { return id == 0 ? 32 : (id == 1 ? 32 : 16); }
+__host__ __device__ constexpr int tile_tj(int id) { return id == 0 ? 8 : (id == 1 ? 4 : 8); }
 
 // ------------------------------------------------------------- halos/BCs --
 template <typename T>
