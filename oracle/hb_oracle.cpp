@@ -945,42 +945,45 @@ void orc_adjoint_columns(void* h, const double* Uin, const double* psi, double J
   std::vector<std::vector<char>> mark(nb);
   for (int b = 0; b < nb; ++b) mark[b].assign(C->B[b].ncell, 0);
   for (int64_t a = 0; a < C->total; ++a) Ud[a] = Dual(base[a], 0.0);
+  std::copy(base.begin(), base.end(), Up.begin());
+  fill_ghosts(*C, Ud.data());
 
-  auto rows_from_tangent = [&](auto tangent_at) {
-    // mark cells with a nonzero tangent, then evaluate rows within radius 2
+  // cells that carry the column's perturbation: the seed itself plus the
+  // ghost cells that the ghost fill derived from it; rows whose stencil
+  // (Chebyshev radius 2) meets one of them are evaluated
+  auto rows_from_tangent = [&](int sb, int64_t sc, auto tangent_at) {
     std::vector<std::array<int, 4>> rows;
+    std::vector<std::vector<char>> seen(nb);
     for (int b = 0; b < nb; ++b) {
       const Block& B = C->B[b];
-      std::fill(mark[b].begin(), mark[b].end(), 0);
-      bool any = false;
-      for (int64_t c = 0; c < B.ncell; ++c) {
-        bool t = false;
-        for (int n = 0; n < C->ns && !t; ++n)
-          for (int v = 0; v < C->nv && !t; ++v) t = tangent_at(C->at(b, n, v, c));
-        if (t) { mark[b][c] = 1; any = true; }
-      }
-      if (!any) continue;
-      int rk = (C->dim == 3) ? 2 : 0;
-      for (int k = 0; k < B.n[2]; ++k)
-        for (int j = 0; j < B.n[1]; ++j)
-          for (int i = 0; i < B.n[0]; ++i) {
-            bool hit = false;
-            for (int dk = -rk; dk <= rk && !hit; ++dk) {
-              int kk = k + dk;
-              if (kk < -B.g[2] || kk >= B.n[2] + B.g[2]) continue;
-              for (int dj = -2; dj <= 2 && !hit; ++dj) {
-                int jj = j + dj;
-                if (jj < -B.g[1] || jj >= B.n[1] + B.g[1]) continue;
-                for (int di = -2; di <= 2 && !hit; ++di) {
-                  int ii = i + di;
-                  if (ii < -B.g[0] || ii >= B.n[0] + B.g[0]) continue;
-                  hit = mark[b][B.cell(ii, jj, kk)] != 0;
-                }
-              }
-            }
-            if (hit) rows.push_back({b, i, j, k});
+      std::vector<std::array<int, 3>> hot;
+      for (int k = -B.g[2]; k < B.n[2] + B.g[2]; ++k)
+        for (int j = -B.g[1]; j < B.n[1] + B.g[1]; ++j)
+          for (int i = -B.g[0]; i < B.n[0] + B.g[0]; ++i) {
+            const bool in = B.interior(i, j, k);
+            const int64_t c = B.cell(i, j, k);
+            if (in && !(b == sb && c == sc)) continue;
+            bool t = false;
+            for (int n = 0; n < C->ns && !t; ++n)
+              for (int v = 0; v < C->nv && !t; ++v) t = tangent_at(C->at(b, n, v, c));
+            if (t) hot.push_back({i, j, k});
           }
+      if (hot.empty()) continue;
+      seen[b].assign(B.ncell, 0);
+      const int rk = (C->dim == 3) ? 2 : 0;
+      for (auto& h : hot)
+        for (int dk = -rk; dk <= rk; ++dk)
+          for (int dj = -2; dj <= 2; ++dj)
+            for (int di = -2; di <= 2; ++di) {
+              int i = h[0] + di, j = h[1] + dj, k = h[2] + dk;
+              if (!B.interior(i, j, k)) continue;
+              int64_t c = B.cell(i, j, k);
+              if (seen[b][c]) continue;
+              seen[b][c] = 1;
+              rows.push_back({b, i, j, k});
+            }
     }
+    std::sort(rows.begin(), rows.end());
     return rows;
   };
 
@@ -991,7 +994,8 @@ void orc_adjoint_columns(void* h, const double* Uin, const double* psi, double J
     if (mode == 0) {
       Ud[a].d = 1.0;
       fill_ghosts(*C, Ud.data());
-      auto rows = rows_from_tangent([&](int64_t x) { return Ud[x].d != 0.0; });
+      auto rows = rows_from_tangent(b, C->B[b].cell(cl[1], cl[2], cl[3]),
+                                    [&](int64_t x) { return Ud[x].d != 0.0; });
       double acc = 0.0;
       for (auto& rw : rows) {
         cell_residual(*C, (const Dual*)Ud.data(), rw[0], rw[1], rw[2], rw[3], rd.data(), (double*)nullptr);
@@ -1008,29 +1012,35 @@ void orc_adjoint_columns(void* h, const double* Uin, const double* psi, double J
       Ud[a].d = 0.0;
       // ghosts keep stale tangents; the next fill overwrites every ghost
     } else {
+      // the rows come from the same structural dependence as the dual mode
+      Ud[a].d = 1.0;
+      fill_ghosts(*C, Ud.data());
+      auto rows = rows_from_tangent(b, C->B[b].cell(cl[1], cl[2], cl[3]),
+                                    [&](int64_t x) { return Ud[x].d != 0.0; });
+      Ud[a].d = 0.0;
       double hh = hstep * std::max(1.0, std::fabs(base[a]));
-      std::copy(base.begin(), base.end(), Up.begin());
-      std::copy(base.begin(), base.end(), Um.begin());
-      Up[a] += hh; Um[a] -= hh;
-      fill_ghosts(*C, Up.data());
-      fill_ghosts(*C, Um.data());
-      auto rows = rows_from_tangent([&](int64_t x) { return Up[x] != Um[x]; });
+      std::vector<double> rp((size_t)rows.size() * C->ns * C->nv), rm(rp.size());
+      double Jp = 0.0, Jm = 0.0;
+      for (int sgn = 0; sgn < 2; ++sgn) {
+        Up[a] = base[a] + (sgn == 0 ? hh : -hh);
+        fill_ghosts(*C, Up.data());
+        std::vector<double>& dst = (sgn == 0) ? rp : rm;
+        for (size_t w = 0; w < rows.size(); ++w)
+          cell_residual(*C, (const double*)Up.data(), rows[w][0], rows[w][1], rows[w][2], rows[w][3],
+                        dst.data() + w * C->ns * C->nv, (double*)nullptr);
+        if (J_seed != 0.0 && C->n_bodies > 0)
+          forces(*C, (const double*)Up.data(), coefp.data(), sgn == 0 ? &Jp : &Jm);
+      }
+      Up[a] = base[a];
       double acc = 0.0;
-      std::vector<double> rm(C->ns * C->nv);
-      for (auto& rw : rows) {
-        cell_residual(*C, (const double*)Up.data(), rw[0], rw[1], rw[2], rw[3], r.data(), (double*)nullptr);
-        cell_residual(*C, (const double*)Um.data(), rw[0], rw[1], rw[2], rw[3], rm.data(), (double*)nullptr);
-        int64_t c = C->B[rw[0]].cell(rw[1], rw[2], rw[3]);
+      for (size_t w = 0; w < rows.size(); ++w) {
+        int64_t c = C->B[rows[w][0]].cell(rows[w][1], rows[w][2], rows[w][3]);
         for (int nn = 0; nn < C->ns; ++nn)
           for (int vv = 0; vv < C->nv; ++vv)
-            acc += psi[C->at(rw[0], nn, vv, c)] * (r[nn * C->nv + vv] - rm[nn * C->nv + vv]);
+            acc += psi[C->at(rows[w][0], nn, vv, c)] *
+                   (rp[w * C->ns * C->nv + nn * C->nv + vv] - rm[w * C->ns * C->nv + nn * C->nv + vv]);
       }
-      if (J_seed != 0.0 && C->n_bodies > 0) {
-        double Jp, Jm;
-        forces(*C, (const double*)Up.data(), coefp.data(), &Jp);
-        forces(*C, (const double*)Um.data(), coefp.data(), &Jm);
-        acc += J_seed * (Jp - Jm);
-      }
+      acc += J_seed * (Jp - Jm);
       out[q] = acc / (2.0 * hh);
     }
   }

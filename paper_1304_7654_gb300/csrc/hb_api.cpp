@@ -13,7 +13,11 @@
 #include <string>
 #include <vector>
 
+#include <algorithm>
+#include <tuple>
+
 #include "../../include/hb.h"
+#include "hb_adjoint.h"
 #include "hb_internal.h"
 
 using hbk::BcRec;
@@ -66,6 +70,17 @@ struct hb_ctx {
   double* d_ring = nullptr;     // [ring][8] norms ring for graph replays
   int ring = 0;
   int* d_err = nullptr;
+  // adjoint (FP64 2D single case): face/cell offsets, wall tags, ghost CSR
+  bool adj_ok = false;
+  std::vector<int64_t> foff_h;
+  int64_t nfaces = 0;
+  int64_t* d_foff = nullptr;
+  int64_t* d_coff = nullptr;
+  int* d_wall = nullptr;
+  double* d_adjbuf = nullptr;
+  hbk::GhostAdjRow* d_grow[3] = {nullptr, nullptr, nullptr};
+  hbk::GhostAdjEntry* d_gent[3] = {nullptr, nullptr, nullptr};
+  int ngrow[3] = {0, 0, 0};
   cudaStream_t cap_stream = nullptr;
   std::map<std::pair<const void*, int>, cudaGraphExec_t> graphs;
   std::map<std::pair<const void*, int>, int64_t> graph_kernels;
@@ -471,6 +486,11 @@ void free_ctx(hb_ctx* c) {
   cudaFree(c->d_done);
   cudaFree(c->d_ring);
   cudaFree(c->d_err);
+  cudaFree(c->d_foff);
+  cudaFree(c->d_coff);
+  cudaFree(c->d_wall);
+  cudaFree(c->d_adjbuf);
+  for (int p = 0; p < 3; ++p) { cudaFree(c->d_grow[p]); cudaFree(c->d_gent[p]); }
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
 }
 
@@ -643,6 +663,63 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
   CK(cudaMalloc(&ctx->d_err, sizeof(int)));
   CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
   CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  // adjoint tables (FP64, 2D, single case)
+  if (ctx->prec == HB_FP64 && ctx->dim == 2 && ctx->cases.size() == 1) {
+    const int nb = (int)ctx->blocks.size();
+    std::vector<int64_t> foff(nb + 1, 0), coff(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) {
+      const BlockDev& B = ctx->blocks[b];
+      foff[b + 1] = foff[b] + (int64_t)(B.n[0] + 1) * B.n[1] + (int64_t)B.n[0] * (B.n[1] + 1);
+      coff[b] = B.goff;
+    }
+    coff[nb] = ctx->geo_cells;
+    ctx->nfaces = foff[nb];
+    ctx->foff_h = foff;
+    std::vector<int> wall((size_t)ctx->nfaces, 0);
+    for (const BcRec& r : Tb.walls) {
+      const BlockDev& B = ctx->blocks[r.blk];
+      const int fi = r.fcell % B.P[0] - 2, fj = r.fcell / B.P[0] - 2;
+      const int64_t nfi = (int64_t)(B.n[0] + 1) * B.n[1];
+      const int64_t f = (r.p == 0) ? foff[r.blk] + (int64_t)fj * (B.n[0] + 1) + fi
+                                   : foff[r.blk] + nfi + (int64_t)fj * B.n[0] + fi;
+      wall[f] = r.sgn * (r.body + 1);
+    }
+    CK(cudaMalloc(&ctx->d_foff, sizeof(int64_t) * (nb + 1)));
+    CK(cudaMemcpy(ctx->d_foff, foff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_coff, sizeof(int64_t) * (nb + 1)));
+    CK(cudaMemcpy(ctx->d_coff, coff.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&ctx->d_wall, sizeof(int) * std::max<int64_t>(1, ctx->nfaces)));
+    CK(cudaMemcpy(ctx->d_wall, wall.data(), sizeof(int) * ctx->nfaces, cudaMemcpyHostToDevice));
+    for (int p = 0; p < ctx->dim; ++p) {
+      // (source block, source cell, kind, record, layer), sorted: a fixed gather order
+      std::vector<std::tuple<int, int, int, int, int>> ge;
+      for (int k = 0; k < (int)Tb.copy[p].size(); ++k)
+        ge.emplace_back(Tb.copy[p][k].src_blk, Tb.copy[p][k].src_cell, 0, k, 0);
+      for (int k = 0; k < (int)Tb.bc[p].size(); ++k) {
+        const BcRec& r = Tb.bc[p][k];
+        if (r.type == HB_BC_FARFIELD) ge.emplace_back(r.blk, r.mcell[0], 1, k, 0);
+        else for (int l = 0; l < 2; ++l) ge.emplace_back(r.blk, r.mcell[l], 2, k, l);
+      }
+      std::sort(ge.begin(), ge.end());
+      std::vector<hbk::GhostAdjRow> rows;
+      std::vector<hbk::GhostAdjEntry> ent;
+      for (size_t q = 0; q < ge.size(); ++q) {
+        const int sb = std::get<0>(ge[q]), sc = std::get<1>(ge[q]);
+        if (rows.empty() || rows.back().src_blk != sb || rows.back().src_cell != sc)
+          rows.push_back({sb, sc, (int)q, (int)q});
+        rows.back().end = (int)q + 1;
+        ent.push_back({std::get<2>(ge[q]), std::get<3>(ge[q]), std::get<4>(ge[q]), 0});
+      }
+      ctx->ngrow[p] = (int)rows.size();
+      if (!rows.empty()) {
+        CK(cudaMalloc(&ctx->d_grow[p], sizeof(hbk::GhostAdjRow) * rows.size()));
+        CK(cudaMemcpy(ctx->d_grow[p], rows.data(), sizeof(hbk::GhostAdjRow) * rows.size(), cudaMemcpyHostToDevice));
+        CK(cudaMalloc(&ctx->d_gent[p], sizeof(hbk::GhostAdjEntry) * ent.size()));
+        CK(cudaMemcpy(ctx->d_gent[p], ent.data(), sizeof(hbk::GhostAdjEntry) * ent.size(), cudaMemcpyHostToDevice));
+      }
+    }
+    ctx->adj_ok = true;
+  }
 #undef CK
   *out = ctx;
   return HB_OK;
@@ -788,12 +865,21 @@ hb_status rk_smooth_impl(hb_ctx* c, T* U, int n_iter, double* norms, cudaStream_
 }
 
 template <typename T>
+hb_status forces_filled(hb_ctx* c, const T* W, double* coef, double* J, cudaStream_t s);
+
+template <typename T>
 hb_status forces_impl(hb_ctx* c, const T* U, double* coef, double* J, cudaStream_t s) {
   T* W = (T*)c->d_A;
   c->n_launch++;
   HB_CUDA(c, hbk::launch_copy(W, U, (int64_t)c->tsize * c->state_size, s));
   hb_status st = halos<T>(c, W, s);
   if (st != HB_OK) return st;
+  return forces_filled<T>(c, W, coef, J, s);
+}
+
+// forces of a state whose ghosts are filled
+template <typename T>
+hb_status forces_filled(hb_ctx* c, const T* W, double* coef, double* J, cudaStream_t s) {
   hbk::ForceParams<T> p;
   p.cases = (const CaseDev<T>*)c->d_cases;
   p.blocks = c->d_blocks;
@@ -897,8 +983,48 @@ hb_status hb_forces(hb_ctx* ctx, const void* U, double* coef, double* J, void* s
 
 hb_status hb_adjoint_residual(hb_ctx* ctx, const void* U, const void* psi, double J_seed, void* r_adj,
                               double* J_dev, void* stream) {
-  (void)U; (void)psi; (void)J_seed; (void)r_adj; (void)J_dev; (void)stream;
-  return fail(ctx, HB_ERR_UNSUPPORTED, "adjoint not built in this library version");
+  if (!ctx || !U || !psi || !r_adj) return fail(ctx, HB_ERR_INVALID_ARG, "null argument");
+  if (!ctx->adj_ok) return fail(ctx, HB_ERR_UNSUPPORTED, "the adjoint needs a single-case FP64 2D context");
+  if (r_adj == U || r_adj == psi) return fail(ctx, HB_ERR_INVALID_ARG, "r_adj must not alias U or psi");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int ns = ctx->cases[0].ns;
+  if (!ctx->d_adjbuf) {
+    cudaError_t e = cudaMalloc(&ctx->d_adjbuf, sizeof(double) * 32 * ctx->nfaces * ns);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(adjoint face buffer)");
+  }
+  double* W = (double*)ctx->d_A;
+  ctx->n_launch++;
+  HB_CUDA(ctx, hbk::launch_copy(W, U, (int64_t)sizeof(double) * ctx->state_size, s));
+  hb_status st = halos<double>(ctx, W, s);
+  if (st != HB_OK) return st;
+  hbk::AdjParams p;
+  p.cases = (const CaseDev<double>*)ctx->d_cases;
+  p.blocks = ctx->d_blocks;
+  p.g = geo_of<double>(ctx);
+  p.nblocks = (int)ctx->blocks.size();
+  p.ns = ns;
+  p.foff = ctx->d_foff;
+  p.coff = ctx->d_coff;
+  p.nfaces = ctx->nfaces;
+  p.ncells_padded = ctx->geo_cells;
+  p.U = W;
+  p.psi = (const double*)psi;
+  p.J_seed = J_seed;
+  p.wall = ctx->d_wall;
+  p.buf = ctx->d_adjbuf;
+  p.out = (double*)ctx->d_B;
+  hbk::AdjGhostPass gp[3];
+  for (int q = 0; q < ctx->dim; ++q) {
+    gp[q].rows = ctx->d_grow[q];
+    gp[q].nrows = ctx->ngrow[q];
+    gp[q].ent = ctx->d_gent[q];
+    gp[q].copies = ctx->d_copy[q];
+    gp[q].bcs = ctx->d_bc[q];
+  }
+  ctx->n_launch += 3 + ctx->dim;
+  HB_CUDA(ctx, hbk::launch_adjoint(p, gp, ctx->dim, (double*)r_adj, s));
+  if (J_dev) return forces_filled<double>(ctx, W, nullptr, J_dev, s);
+  return HB_OK;
 }
 
 hb_status hb_set_timing(hb_ctx* ctx, int enable) {
