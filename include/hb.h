@@ -170,10 +170,16 @@ hb_status hb_residual(hb_ctx* ctx, const void* U, void* R, void* stream);
 
 /* n_iter iterations of the 4-stage Runge-Kutta smoother (coefficients 1/4,
  * 1/3, 1/2, 1) with local pseudo-time steps, in place on U.  norms_dev, if
- * not NULL: device FP64 [n_iter][nv], the RMS over interior cells and
- * snapshots of R/V per variable at the first stage of each iteration,
- * summed in a fixed order (bitwise reproducible).  Non-finite norms latch
- * HB_ERR_NONFINITE (read with hb_sync_status). */
+ * not NULL: device FP64 [n_iter][n_cases][nv] (n_cases = 1 for hb_create),
+ * the RMS over interior cells and snapshots of R/V per variable at the first
+ * stage of each iteration, summed in a fixed order (bitwise reproducible).
+ * Non-finite norms latch HB_ERR_NONFINITE (read with hb_sync_status).
+ * Depending on the context's tuning, each chunk of up to 64 iterations runs
+ * either as one launch per phase or as one persistent cooperative launch
+ * (all cases, all phases, bounded-spin grid barriers: a barrier that waits
+ * longer than HB_BARRIER_TIMEOUT_MS, default 2000, latches HB_ERR_TIMEOUT
+ * and the launch returns); chunks are captured and replayed as CUDA graphs
+ * where the driver allows it. */
 hb_status hb_rk_smooth(hb_ctx* ctx, void* U, int n_iter, double* norms_dev, void* stream);
 
 /* Force coefficients of every body at every snapshot, packed
@@ -191,6 +197,17 @@ hb_status hb_forces(hb_ctx* ctx, const void* U, double* coeffs_dev, double* J_de
  * entries ignored).  Supported for HB_FP64 2D contexts. */
 hb_status hb_adjoint_residual(hb_ctx* ctx, const void* U, const void* psi, double J_seed,
                               void* r_adj, double* J_dev, void* stream);
+
+/* Autotuner: time `iters` RK iterations of every compiled combination of
+ * driver (one launch per phase, or persistent) and tile shape (32x8, 32x4,
+ * 16x8 cells) on a scratch copy of U, keep the fastest, and record it in the
+ * cache file ($HB_TUNE_CACHE, default ~/.cache/hbgpu_autotune.txt) keyed by
+ * the case signature; hb_create reads that cache.  U is not modified.
+ * Synchronises `stream`.  hb_set_tuning forces a choice (mode 0: per-phase
+ * launches, 1: persistent); hb_get_tuning reads it. */
+hb_status hb_autotune(hb_ctx* ctx, const void* U, int iters, void* stream);
+hb_status hb_set_tuning(hb_ctx* ctx, int mode, int TI, int TJ);
+hb_status hb_get_tuning(const hb_ctx* ctx, int* mode, int* TI, int* TJ);
 
 /* Benchmark timing.  While enabled, every launch of the tile kernels
  * (residual / RK stage: class 0) and of the halo kernels (class 1) made

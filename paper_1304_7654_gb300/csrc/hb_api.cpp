@@ -6,8 +6,11 @@
 // i, then j, then k, so block corners take their diagonal neighbours), builds
 // the tile work list and allocates the library-owned workspace.  Every entry
 // point only enqueues kernels on the caller's stream.
+#include <sys/stat.h>
+
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -49,7 +52,19 @@ struct hb_ctx {
   int64_t total_cells = 0;
   int ns_max = 1;
   int TI = 32, TJ = 8, ti_shift = 5;
+  int mode = 0;                 // 0: one launch per stage, 1: persistent driver
   std::vector<int4> tiles;
+  int max_tiles = 0;            // capacity of the tile-sized device buffers
+  int* d_order = nullptr;       // claim order for the persistent driver
+  unsigned int* d_work = nullptr;   // [kMaxK * 4] claim counters
+  unsigned int* d_bar = nullptr;    // barrier words
+  int* d_case_tile0 = nullptr;
+  int* d_case_ntiles = nullptr;
+  double* d_case_inv = nullptr;
+  long long timeout_ns = 2000000000LL;
+  int skip_cta = -1;
+  int persist_graph = -1;       // -1 untested, 0 capture unsupported, 1 captured
+  std::string tune_key;
   // device
   void* d_cases = nullptr;
   BlockDev* d_blocks = nullptr;
@@ -82,7 +97,7 @@ struct hb_ctx {
   hbk::GhostAdjEntry* d_gent[3] = {nullptr, nullptr, nullptr};
   int ngrow[3] = {0, 0, 0};
   cudaStream_t cap_stream = nullptr;
-  std::map<std::pair<const void*, int>, cudaGraphExec_t> graphs;
+  std::map<std::pair<const void*, int>, cudaGraphExec_t> graphs;   // key: (U, K * 8 + mode)
   std::map<std::pair<const void*, int>, int64_t> graph_kernels;
   // benchmark timing
   int timing = 0;
@@ -486,12 +501,113 @@ void free_ctx(hb_ctx* c) {
   cudaFree(c->d_done);
   cudaFree(c->d_ring);
   cudaFree(c->d_err);
+  cudaFree(c->d_order);
+  cudaFree(c->d_work);
+  cudaFree(c->d_bar);
+  cudaFree(c->d_case_tile0);
+  cudaFree(c->d_case_ntiles);
+  cudaFree(c->d_case_inv);
   cudaFree(c->d_foff);
   cudaFree(c->d_coff);
   cudaFree(c->d_wall);
   cudaFree(c->d_adjbuf);
   for (int p = 0; p < 3; ++p) { cudaFree(c->d_grow[p]); cudaFree(c->d_gent[p]); }
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+}
+
+constexpr int kMaxK = 64;   // iterations per persistent launch / graph
+
+// Tile work list for shape TI x TJ: tiles of every case in case order, the
+// claim order (cost = snapshots x cells, largest first) and per-case ranges.
+hb_status rebuild_tiles(hb_ctx* c, int TI, int TJ) {
+  std::vector<int4> tiles;
+  std::vector<int> t0(c->cases.size()), nt(c->cases.size());
+  std::vector<double> inv(c->cases.size());
+  std::vector<std::pair<long long, int>> cost;
+  for (size_t k = 0; k < c->cases.size(); ++k) {
+    CaseHost& ch = c->cases[k];
+    ch.tile0 = (int)tiles.size();
+    for (int b = 0; b < ch.nblocks; ++b) {
+      const BlockDev& B = c->blocks[ch.block0 + b];
+      for (int j = 0; j < B.n[1]; j += TJ)
+        for (int i = 0; i < B.n[0]; i += TI) {
+          const long long cells = (long long)std::min(TI, B.n[0] - i) * std::min(TJ, B.n[1] - j);
+          cost.push_back({-(cells * ch.ns), (int)tiles.size()});
+          tiles.push_back(make_int4(ch.block0 + b, i, j, 0));
+        }
+    }
+    ch.ntiles = (int)tiles.size() - ch.tile0;
+    t0[k] = ch.tile0;
+    nt[k] = ch.ntiles;
+    inv[k] = 1.0 / ((double)ch.cells * ch.ns);
+  }
+  std::stable_sort(cost.begin(), cost.end());
+  std::vector<int> order(cost.size());
+  for (size_t q = 0; q < cost.size(); ++q) order[q] = cost[q].second;
+  const int n = (int)tiles.size();
+  if (n > c->max_tiles) {
+    cudaFree(c->d_tiles);
+    cudaFree(c->d_order);
+    cudaFree(c->d_partials);
+    c->d_tiles = nullptr; c->d_order = nullptr; c->d_partials = nullptr;
+    HB_CUDA(c, cudaMalloc(&c->d_tiles, sizeof(int4) * std::max(1, n)));
+    HB_CUDA(c, cudaMalloc(&c->d_order, sizeof(int) * std::max(1, n)));
+    HB_CUDA(c, cudaMalloc(&c->d_partials, sizeof(double) * 8 * std::max(1, n)));
+    c->max_tiles = n;
+  }
+  HB_CUDA(c, cudaMemcpy(c->d_tiles, tiles.data(), sizeof(int4) * n, cudaMemcpyHostToDevice));
+  HB_CUDA(c, cudaMemcpy(c->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  if (!c->d_case_tile0) {
+    HB_CUDA(c, cudaMalloc(&c->d_case_tile0, sizeof(int) * c->cases.size()));
+    HB_CUDA(c, cudaMalloc(&c->d_case_ntiles, sizeof(int) * c->cases.size()));
+    HB_CUDA(c, cudaMalloc(&c->d_case_inv, sizeof(double) * c->cases.size()));
+  }
+  HB_CUDA(c, cudaMemcpy(c->d_case_tile0, t0.data(), sizeof(int) * t0.size(), cudaMemcpyHostToDevice));
+  HB_CUDA(c, cudaMemcpy(c->d_case_ntiles, nt.data(), sizeof(int) * nt.size(), cudaMemcpyHostToDevice));
+  HB_CUDA(c, cudaMemcpy(c->d_case_inv, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice));
+  c->tiles = tiles;
+  c->TI = TI;
+  c->TJ = TJ;
+  c->ti_shift = 0;
+  while ((1 << c->ti_shift) < TI) ++c->ti_shift;
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  c->graph_kernels.clear();
+  return HB_OK;
+}
+
+// autotune cache: one line per signature, "key mode TI TJ"
+std::string tune_cache_path() {
+  const char* e = getenv("HB_TUNE_CACHE");
+  if (e && *e) return e;
+  const char* h = getenv("HOME");
+  return std::string(h && *h ? h : "/tmp") + "/.cache/hbgpu_autotune.txt";
+}
+
+bool tune_lookup(const std::string& key, int* mode, int* TI, int* TJ) {
+  FILE* f = fopen(tune_cache_path().c_str(), "r");
+  if (!f) return false;
+  char k[512];
+  int m, a, b;
+  bool found = false;
+  while (fscanf(f, "%511s %d %d %d", k, &m, &a, &b) == 4)
+    if (key == k) { *mode = m; *TI = a; *TJ = b; found = true; }
+  fclose(f);
+  return found;
+}
+
+void tune_store(const std::string& key, int mode, int TI, int TJ) {
+  const std::string path = tune_cache_path();
+  const size_t slash = path.rfind('/');
+  if (slash != std::string::npos) {
+    std::string dir = path.substr(0, slash);
+    for (size_t q = 1; q <= dir.size(); ++q)
+      if (q == dir.size() || dir[q] == '/') mkdir(dir.substr(0, q).c_str(), 0755);
+  }
+  FILE* f = fopen(path.c_str(), "a");
+  if (!f) return;
+  fprintf(f, "%s %d %d %d\n", key.c_str(), mode, TI, TJ);
+  fclose(f);
 }
 
 hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
@@ -572,16 +688,6 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
     hb_status s = build_tables(ctx, ch, Tb);
     if (s != HB_OK) return bad(s, ctx->err);
   }
-  // tiles
-  for (auto& ch : ctx->cases) {
-    ch.tile0 = (int)ctx->tiles.size();
-    for (int b = 0; b < ch.nblocks; ++b) {
-      const BlockDev& B = ctx->blocks[ch.block0 + b];
-      for (int j = 0; j < B.n[1]; j += ctx->TJ)
-        for (int i = 0; i < B.n[0]; i += ctx->TI) ctx->tiles.push_back(make_int4(ch.block0 + b, i, j, 0));
-    }
-    ch.ntiles = (int)ctx->tiles.size() - ch.tile0;
-  }
   // geometry (FP64 on the host, rounded once)
   std::vector<double> G((size_t)hbk::G_NQ * ctx->geo_cells, 0.0);
   for (auto& ch : ctx->cases)
@@ -630,8 +736,6 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
   CK(cudaMemcpy(ctx->d_cases, cbuf.data(), cbuf.size(), cudaMemcpyHostToDevice));
   CK(cudaMalloc(&ctx->d_blocks, sizeof(BlockDev) * ctx->blocks.size()));
   CK(cudaMemcpy(ctx->d_blocks, ctx->blocks.data(), sizeof(BlockDev) * ctx->blocks.size(), cudaMemcpyHostToDevice));
-  CK(cudaMalloc(&ctx->d_tiles, sizeof(int4) * std::max<size_t>(1, ctx->tiles.size())));
-  CK(cudaMemcpy(ctx->d_tiles, ctx->tiles.data(), sizeof(int4) * ctx->tiles.size(), cudaMemcpyHostToDevice));
   for (int p = 0; p < 3; ++p) {
     ctx->ncopy[p] = (int)Tb.copy[p].size();
     ctx->nbc[p] = (int)Tb.bc[p].size();
@@ -657,9 +761,35 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
   CK(cudaMalloc(&ctx->d_B, ts * ctx->state_size));
   CK(cudaMemset(ctx->d_A, 0, ts * ctx->state_size));
   CK(cudaMemset(ctx->d_B, 0, ts * ctx->state_size));
-  CK(cudaMalloc(&ctx->d_partials, sizeof(double) * 8 * std::max<size_t>(1, ctx->tiles.size())));
-  ctx->ring = 64;
-  CK(cudaMalloc(&ctx->d_ring, sizeof(double) * 8 * ctx->ring));
+  ctx->ring = kMaxK;
+  CK(cudaMalloc(&ctx->d_ring, sizeof(double) * 8 * ctx->ring * ctx->cases.size()));
+  CK(cudaMalloc(&ctx->d_work, sizeof(unsigned int) * 4 * kMaxK));
+  CK(cudaMalloc(&ctx->d_bar, sizeof(unsigned int) * 4));
+  CK(cudaMemset(ctx->d_bar, 0, sizeof(unsigned int) * 4));
+  {
+    const char* e = getenv("HB_BARRIER_TIMEOUT_MS");
+    if (e && *e) ctx->timeout_ns = (long long)(atof(e) * 1.0e6);
+    e = getenv("HB_TEST_SKIP_BARRIER_CTA");
+    if (e && *e) ctx->skip_cta = atoi(e);
+  }
+  // tuning: cached choice for this signature, else the defaults
+  {
+    std::string key = "d" + std::to_string(ctx->dim) + "_p" + std::to_string(ctx->prec) + "_v" +
+                      std::to_string(ctx->viscous) + "_c" + std::to_string(ctx->cases.size()) + "_n" +
+                      std::to_string(ctx->total_cells) + "_b" + std::to_string(ctx->blocks.size()) + "_s";
+    for (auto& ch : ctx->cases) key += std::to_string(ch.ns);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    key += "_sm" + std::to_string(sms);
+    ctx->tune_key = key.substr(0, 500);
+    int m = (ctx->cases.size() > 1 && ctx->prec == HB_FP32) ? 1 : 0, a = 32, b = 8;
+    int mm, aa, bb;
+    if (tune_lookup(ctx->tune_key, &mm, &aa, &bb)) { m = mm; a = aa; b = bb; }
+    ctx->mode = m;
+    hb_status st = rebuild_tiles(ctx, a, b);
+    if (st != HB_OK) return bad(st, ctx->err);
+  }
   CK(cudaMalloc(&ctx->d_err, sizeof(int)));
   CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
   CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
@@ -807,61 +937,181 @@ hb_status rk_iteration(hb_ctx* c, T* U, double* norm_out, cudaStream_t s) {
     r = stage_all<T>(c, p, 1, s);
     if (r != HB_OK) return r;
     if (st == 0) {
-      // norms per case, fixed order; batched contexts report the first case
-      const CaseHost& ch = c->cases[0];
-      c->n_launch++;
-      HB_CUDA(c, hbk::launch_norm_finish(c->d_partials + (size_t)8 * ch.tile0, ch.ntiles, c->nv,
-                                         1.0 / ((double)ch.cells * ch.ns), norm_out, c->d_err, s));
+      // norms per case, fixed order, into norm_out[case][8]
+      for (size_t k = 0; k < c->cases.size(); ++k) {
+        const CaseHost& ch = c->cases[k];
+        c->n_launch++;
+        HB_CUDA(c, hbk::launch_norm_finish(c->d_partials + (size_t)8 * ch.tile0, ch.ntiles, c->nv,
+                                           1.0 / ((double)ch.cells * ch.ns), norm_out + 8 * k, c->d_err, s));
+      }
     }
+  }
+  return HB_OK;
+}
+
+// one persistent launch of K iterations (norms into the ring)
+template <typename T>
+hb_status persist_chunk(hb_ctx* c, T* U, int K, cudaStream_t s) {
+  static const double alpha[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
+  HB_CUDA(c, cudaMemsetAsync(c->d_work, 0, sizeof(unsigned int) * 4 * K, s));
+  HB_CUDA(c, cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned int) * 4, s));
+  hbk::PersistParams<T> p;
+  memset(&p, 0, sizeof(p));
+  T* A = (T*)c->d_A;
+  T* Bf = (T*)c->d_B;
+  T* in[4] = {U, A, Bf, A};
+  T* out[4] = {A, Bf, A, U};
+  for (int st = 0; st < 4; ++st) {
+    p.st[st] = stage_params<T>(c);
+    p.st[st].tiles = c->d_tiles;
+    p.st[st].ntiles = (int)c->tiles.size();
+    p.st[st].Uprev = in[st];
+    p.st[st].U0 = U;
+    p.st[st].Unext = out[st];
+    p.st[st].alpha = (T)alpha[st];
+    p.st[st].partials = (st == 0) ? c->d_partials : nullptr;
+  }
+  for (int pass = 0; pass < c->dim; ++pass) {
+    hbk::HaloParams<T>& h = p.halo[pass];
+    h.cases = (const CaseDev<T>*)c->d_cases;
+    h.blocks = c->d_blocks;
+    h.g = geo_of<T>(c);
+    h.U = nullptr;
+    h.copies = c->d_copy[pass];
+    h.ncopy = c->ncopy[pass];
+    h.bcs = c->d_bc[pass];
+    h.nbc = c->nbc[pass];
+    h.ns_max = c->ns_max;
+  }
+  p.dim = c->dim;
+  p.order = c->d_order;
+  p.ntiles = (int)c->tiles.size();
+  p.work = c->d_work;
+  p.bar = c->d_bar;
+  p.err = c->d_err;
+  p.K = K;
+  p.ncases = (int)c->cases.size();
+  p.case_tile0 = c->d_case_tile0;
+  p.case_ntiles = c->d_case_ntiles;
+  p.case_inv = c->d_case_inv;
+  p.norms = c->d_ring;
+  p.timeout_ns = c->timeout_ns;
+  p.skip_cta = c->skip_cta;
+  TimedScope ts(c, 0, s);
+  int grid = 0;
+  HB_CUDA(c, hbk::launch_persist<T>(p, c->viscous, c->TI, c->TJ, s, &grid));
+  return HB_OK;
+}
+
+// ring [K][ncases][8] -> user norms [K][ncases][nv]
+hb_status copy_norms(hb_ctx* c, double* norms, int done, int K, cudaStream_t s) {
+  if (!norms) return HB_OK;
+  const size_t nc = c->cases.size();
+  HB_CUDA(c, cudaMemcpy2DAsync(norms + (size_t)done * nc * c->nv, sizeof(double) * c->nv, c->d_ring,
+                               sizeof(double) * 8, sizeof(double) * c->nv, (size_t)K * nc,
+                               cudaMemcpyDeviceToDevice, s));
+  return HB_OK;
+}
+
+template <typename T>
+hb_status rk_chunk_direct(hb_ctx* c, T* U, int K, cudaStream_t s) {
+  if (c->mode == 1 && hbk::persist_available<T>(c->TI, c->TJ)) return persist_chunk<T>(c, U, K, s);
+  const size_t nc = c->cases.size();
+  for (int k = 0; k < K; ++k) {
+    hb_status r = rk_iteration<T>(c, U, c->d_ring + 8 * nc * k, s);
+    if (r != HB_OK) return r;
   }
   return HB_OK;
 }
 
 template <typename T>
 hb_status rk_smooth_impl(hb_ctx* c, T* U, int n_iter, double* norms, cudaStream_t s) {
-  const int K = std::min(n_iter, c->ring);
   int done = 0;
-  // full chunks of K iterations replay one captured graph
-  if (n_iter >= 2) {
-    auto key = std::make_pair((const void*)U, K);
-    auto it = c->graphs.find(key);
-    if (it == c->graphs.end()) {
-      cudaGraph_t g;
-      HB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
-      hb_status r = HB_OK;
-      c->capturing = true;
-      const int64_t n0 = c->n_launch;
-      for (int k = 0; k < K && r == HB_OK; ++k) r = rk_iteration<T>(c, U, c->d_ring + 8 * k, c->cap_stream);
-      c->capturing = false;
-      c->graph_kernels[key] = c->n_launch - n0;
-      c->n_launch = n0;
-      cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  while (done < n_iter) {
+    const int K = std::min(n_iter - done, c->ring);
+    const bool persist = c->mode == 1 && hbk::persist_available<T>(c->TI, c->TJ);
+    // chunks of two or more iterations (or any persistent chunk) replay a
+    // captured graph; a persistent chunk runs directly if capture fails
+    bool use_graph = (K >= 2 || persist) && !(persist && c->persist_graph == 0);
+    if (use_graph) {
+      auto key = std::make_pair((const void*)U, K * 8 + c->mode);
+      auto it = c->graphs.find(key);
+      if (it == c->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ex = nullptr;
+        HB_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
+        c->capturing = true;
+        const int64_t n0 = c->n_launch;
+        hb_status r = rk_chunk_direct<T>(c, U, K, c->cap_stream);
+        c->capturing = false;
+        const int64_t nk = c->n_launch - n0;
+        c->n_launch = n0;
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+        if (r == HB_OK && e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (r != HB_OK || e != cudaSuccess) {
+          cudaGetLastError();
+          if (!persist) return r != HB_OK ? r : cuda_fail(c, e, "graph capture");
+          c->persist_graph = 0;      // cooperative launch not capturable here
+          use_graph = false;
+        } else {
+          if (persist) c->persist_graph = 1;
+          it = c->graphs.emplace(key, ex).first;
+          c->graph_kernels[key] = nk;
+        }
+      }
+      if (use_graph) {
+        c->n_launch += c->graph_kernels[key];
+        HB_CUDA(c, cudaGraphLaunch(it->second, s));
+      }
+    }
+    if (!use_graph) {
+      hb_status r = rk_chunk_direct<T>(c, U, K, s);
       if (r != HB_OK) return r;
-      if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
-      cudaGraphExec_t ex;
-      e = cudaGraphInstantiate(&ex, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
-      it = c->graphs.emplace(key, ex).first;
     }
-    while (n_iter - done >= K) {
-      c->n_launch += c->graph_kernels[key];
-      HB_CUDA(c, cudaGraphLaunch(it->second, s));
-      if (norms)
-        HB_CUDA(c, cudaMemcpy2DAsync(norms + (size_t)done * c->nv, sizeof(double) * c->nv, c->d_ring,
-                                     sizeof(double) * 8, sizeof(double) * c->nv, K,
-                                     cudaMemcpyDeviceToDevice, s));
-      done += K;
-    }
-  }
-  for (; done < n_iter; ++done) {
-    hb_status r = rk_iteration<T>(c, U, c->d_ring, s);
+    hb_status r = copy_norms(c, norms, done, K, s);
     if (r != HB_OK) return r;
-    if (norms)
-      HB_CUDA(c, cudaMemcpyAsync(norms + (size_t)done * c->nv, c->d_ring, sizeof(double) * c->nv,
-                                 cudaMemcpyDeviceToDevice, s));
+    done += K;
   }
   return HB_OK;
+}
+
+// autotuner: time every compiled (driver, tile shape) on a copy of U
+template <typename T>
+hb_status autotune_impl(hb_ctx* c, const T* U, int iters, cudaStream_t s) {
+  void* tmp = nullptr;
+  HB_CUDA(c, cudaMalloc(&tmp, c->tsize * c->state_size));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bm = c->mode, bi = c->TI, bj = c->TJ;
+  hb_status st = HB_OK;
+  const int shapes[3][2] = {{32, 8}, {32, 4}, {16, 8}};
+  for (int m = 0; m < 2 && st == HB_OK; ++m)
+    for (int q = 0; q < 3 && st == HB_OK; ++q) {
+      if (m == 1 && !hbk::persist_available<T>(shapes[q][0], shapes[q][1])) continue;
+      if ((st = rebuild_tiles(c, shapes[q][0], shapes[q][1])) != HB_OK) break;
+      c->mode = m;
+      cudaMemcpyAsync(tmp, U, c->tsize * c->state_size, cudaMemcpyDeviceToDevice, s);
+      if ((st = rk_smooth_impl<T>(c, (T*)tmp, iters, nullptr, s)) != HB_OK) break;   // warm-up, graphs
+      cudaEventRecord(e0, s);
+      if ((st = rk_smooth_impl<T>(c, (T*)tmp, iters, nullptr, s)) != HB_OK) break;
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; bm = m; bi = shapes[q][0]; bj = shapes[q][1]; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  cudaFree(tmp);
+  if (st != HB_OK) return st;
+  st = rebuild_tiles(c, bi, bj);
+  c->mode = bm;
+  if (st == HB_OK) tune_store(c->tune_key, bm, bi, bj);
+  return st;
 }
 
 template <typename T>
@@ -1024,6 +1274,34 @@ hb_status hb_adjoint_residual(hb_ctx* ctx, const void* U, const void* psi, doubl
   ctx->n_launch += 3 + ctx->dim;
   HB_CUDA(ctx, hbk::launch_adjoint(p, gp, ctx->dim, (double*)r_adj, s));
   if (J_dev) return forces_filled<double>(ctx, W, nullptr, J_dev, s);
+  return HB_OK;
+}
+
+hb_status hb_autotune(hb_ctx* ctx, const void* U, int iters, void* stream) {
+  if (!ctx || !U || iters < 1) return fail(ctx, HB_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  return ctx->prec == HB_FP32 ? autotune_impl<float>(ctx, (const float*)U, iters, s)
+                              : autotune_impl<double>(ctx, (const double*)U, iters, s);
+}
+
+hb_status hb_set_tuning(hb_ctx* ctx, int mode, int TI, int TJ) {
+  if (!ctx || mode < 0 || mode > 1) return fail(ctx, HB_ERR_INVALID_ARG, "bad tuning");
+  const bool ok = (TI == 32 && TJ == 8) || (TI == 32 && TJ == 4) || (TI == 16 && TJ == 8);
+  if (!ok) return fail(ctx, HB_ERR_UNSUPPORTED, "tile shape not built");
+  const bool pok = ctx->prec == HB_FP32 ? hbk::persist_available<float>(TI, TJ)
+                                        : hbk::persist_available<double>(TI, TJ);
+  if (mode == 1 && !pok) return fail(ctx, HB_ERR_UNSUPPORTED, "persistent driver not built for this shape");
+  hb_status st = rebuild_tiles(ctx, TI, TJ);
+  if (st != HB_OK) return st;
+  ctx->mode = mode;
+  return HB_OK;
+}
+
+hb_status hb_get_tuning(const hb_ctx* ctx, int* mode, int* TI, int* TJ) {
+  if (!ctx) return HB_ERR_INVALID_ARG;
+  if (mode) *mode = ctx->mode;
+  if (TI) *TI = ctx->TI;
+  if (TJ) *TJ = ctx->TJ;
   return HB_OK;
 }
 

@@ -113,6 +113,29 @@ struct ForceParams {
   unsigned int* done;       // completion counter (zero between launches)
 };
 
+// One persistent launch advancing K RK iterations of every case: per stage,
+// the halo passes then all tiles (claimed dynamically in cost order), each
+// phase closed by a bounded-spin grid barrier.
+template <typename T>
+struct PersistParams {
+  StageParams<T> st[4];     // per RK stage (tiles, Uprev, U0, Unext, alpha, partials)
+  HaloParams<T> halo[3];    // per pass; the kernel points U at the stage input
+  int dim;
+  const int* order;         // tile indices in claim order
+  int ntiles;
+  unsigned int* work;       // [K * 4] claim counters, zero at launch
+  unsigned int* bar;        // [0] arrivals, [1] generation, [2] abort flag; zero at launch
+  int* err;                 // device error word
+  int K;
+  int ncases;
+  const int* case_tile0;
+  const int* case_ntiles;
+  const double* case_inv;   // 1 / (cells * snapshots) per case
+  double* norms;            // [K][ncases][8] or null
+  long long timeout_ns;     // barrier wait limit
+  int skip_cta;             // test hook: this CTA does not arrive at the first barrier (-1: none)
+};
+
 // launchers (defined per precision in hb_kernels_f32.cu / hb_kernels_f64.cu)
 template <typename T>
 cudaError_t launch_halo(const HaloParams<T>& p, cudaStream_t s);
@@ -126,6 +149,12 @@ template <typename T>
 cudaError_t launch_forces(const ForceParams<T>& p, cudaStream_t s);
 template <typename T>
 cudaError_t stage_smem_bytes(int TI, int TJ, size_t* bytes);
+
+template <typename T>
+cudaError_t launch_persist(const PersistParams<T>& p, int viscous, int TI, int TJ, cudaStream_t s,
+                           int* grid_out);
+template <typename T>
+bool persist_available(int TI, int TJ);
 
 cudaError_t launch_norm_finish(const double* partials, int ntiles, int nv, double inv_count,
                                double* out, int* err, cudaStream_t s);

@@ -495,12 +495,11 @@ __device__ __forceinline__ void freestream_at(const CaseDev<T>* C, int n, T x, T
   if (C->ubc == 2) W[2] += C->ubc_amp * C->mach * sin(C->tn[n] - C->omega * x / C->mach);
 }
 
-// one thread per (record, snapshot), snapshot-major so that neighbouring
+// one work item per (record, snapshot), snapshot-major so that neighbouring
 // threads touch neighbouring cells
 template <typename T, int DIM>
-__global__ void halo_kernel(HaloParams<T> p) {
+__device__ __forceinline__ void halo_item(const HaloParams<T>& p, int64_t gid) {
   constexpr int NV = DIM + 2;
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nc = (int64_t)p.ncopy * p.ns_max;
   if (gid < nc) {
     const int n = (int)(gid / p.ncopy), rec = (int)(gid % p.ncopy);
@@ -595,6 +594,11 @@ __global__ void halo_kernel(HaloParams<T> p) {
       store(r.gcell[l], Wg);
     }
   }
+}
+
+template <typename T, int DIM>
+__global__ void halo_kernel(HaloParams<T> p) {
+  halo_item<T, DIM>(p, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------- initial state --

@@ -96,6 +96,9 @@ def load(path: str | None = None):
     lib.hb_adjoint_residual.argtypes = [_vp, _vp, _vp, ct.c_double, _vp, _vp, _vp]
     lib.hb_sync_status.argtypes = [_vp, _vp]
     lib.hb_set_timing.argtypes = [_vp, ct.c_int]
+    lib.hb_autotune.argtypes = [_vp, _vp, ct.c_int, _vp]
+    lib.hb_set_tuning.argtypes = [_vp, ct.c_int, ct.c_int, ct.c_int]
+    lib.hb_get_tuning.argtypes = [_vp, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]
     lib.hb_kernel_stats.argtypes = [_vp, ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64),
                                     ct.c_int]
     lib.hb_residual_norms_noalloc.argtypes = [_vp, _vp, ct.c_int, ct.c_int64, ct.c_int, ct.c_int,
@@ -165,6 +168,7 @@ class HBContext:
         self.prec = HB_FP32 if prec in ("fp32", HB_FP32) else HB_FP64
         cases = case if isinstance(case, (list, tuple)) else [case]
         self.cases = list(cases)
+        self.is_batch = isinstance(case, (list, tuple))
         descs, keep = [], []
         for c in cases:
             d, k = _desc(c, self.prec)
@@ -263,10 +267,29 @@ class HBContext:
         return R
 
     def rk_smooth(self, U, n_iter, norms=True):
+        """n_iter RK iterations in place; returns FP64 norms [n_iter][nv]
+        (single case) or [n_iter][n_cases][nv] (batch)."""
         import torch
-        out = torch.zeros((max(n_iter, 1), self.nv), dtype=torch.float64, device=U.device) if norms else None
+        nc = len(self.cases)
+        out = (torch.zeros((max(n_iter, 1), nc, self.nv), dtype=torch.float64, device=U.device)
+               if norms else None)
         self._check(self.lib.hb_rk_smooth(self.h, _ptr(U), int(n_iter), _ptr(out), _stream()))
-        return out[:n_iter] if norms else None
+        if not norms:
+            return None
+        out = out[:n_iter]
+        return out[:, 0] if nc == 1 and not self.is_batch else out
+
+    def autotune(self, U, iters=3):
+        self._check(self.lib.hb_autotune(self.h, _ptr(U), int(iters), _stream()))
+        return self.tuning()
+
+    def set_tuning(self, mode, TI=32, TJ=8):
+        self._check(self.lib.hb_set_tuning(self.h, int(mode), int(TI), int(TJ)))
+
+    def tuning(self):
+        m, a, b = ct.c_int(), ct.c_int(), ct.c_int()
+        self._check(self.lib.hb_get_tuning(self.h, ct.byref(m), ct.byref(a), ct.byref(b)))
+        return int(m.value), int(a.value), int(b.value)
 
     def rk_smooth_into(self, U, n_iter, norms=None):
         """hb_rk_smooth with a caller-provided FP64 [n_iter][nv] norms tensor (or None)."""
