@@ -50,7 +50,7 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -65,7 +65,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             threading.Thread(target=self._read, daemon=True).start()
         except Exception:
             self.proc = None
@@ -172,6 +172,18 @@ def algorithmic_bytes_per_unit(nv, s, moving, viscous, ns):
     return state + geo * s / ns
 
 
+def roofline(peaks, src, bpu_stage, cells_snaps, mode, launch_ms, kernel, traffic):
+    """Dominant kernel: the tile kernel (one RK stage per launch) or the
+    persistent driver (one RK iteration = 4 stages per launch)."""
+    stages = 4 if mode == 1 else 1
+    units = cells_snaps * stages
+    achieved = bpu_stage * units / (launch_ms * 1e-3) / 1e9 if launch_ms > 0 else 0.0
+    return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kernel,
+            "peak_source": src, "bytes_per_unit": bpu_stage, "unit_def": "cell-snapshot-stage",
+            "units_per_launch": units, "launch_ms": launch_ms}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -194,11 +206,16 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def run_prec(prec, steps, warmup, timing=True):
+    def run_prec(prec, steps, warmup, timing=True, tune=True):
         ctx = hb.HBContext(cs, prec)
         U = ctx.new_state(dev)
         noise = torch.as_tensor(C.noise(cs), device=dev)
         ctx.init_state(U, noise, 0.01)
+        if tune and args.tuning:
+            m, ti, tj = (int(x) for x in args.tuning.split(","))
+            ctx.set_tuning(m, ti, tj)
+        elif tune:
+            ctx.autotune(U, iters=3)
         norms = torch.zeros((1, cs.nv), dtype=torch.float64, device=dev)
         coef = torch.zeros((cs.n_snap, cs.n_bodies, 3), dtype=torch.float64, device=dev)
         J = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -235,15 +252,17 @@ def run_ours(args):
         ctx.set_timing(False)
         st = ctx.sync_status()
         return dict(ms=ms, wall=wall, tile_ms=tile_ms, tile_n=tile_n, halo_ms=halo_ms, halo_n=halo_n,
-                    launches=launches, status=st, ctx=ctx, U=U)
+                    launches=launches, status=st, ctx=ctx, U=U, tuning=ctx.tuning())
 
     # FP32 flux path with FP64 norms and force sums (headline)
     clocks = ClockSampler(local)
     clocks.start()
     r32 = run_prec("fp32", args.steps, args.warmup)
     clk = clocks.stop()
-    # FP64 plain path on the same workload, for comparison
-    r64 = run_prec("fp64", args.fp64_steps, 2)
+    # FP64 plain path on the same workload, for comparison (one launch per phase)
+    r64 = run_prec("fp64", args.fp64_steps, 2, tune=False)
+    batch = run_batch(args, dev) if not args.no_batch else None
+    adj = adjoint_ratio(dev) if not args.no_adjoint else None
 
     # e2e: host buffers in pinned memory, H2D of the state and D2H of the
     # step's results (norms, force coefficients, J) inside the timed region
@@ -294,18 +313,12 @@ def run_ours(args):
     v64 = units_per_step / (r64["ms"] / args.fp64_steps * 1e-3)
 
     peaks, src = _peaks()
-    s = 4
-    bpu = algorithmic_bytes_per_unit(cs.nv, s, True, True, cs.n_snap)
-    units_per_launch = cs.n_cells * cs.n_snap
+    bpu = algorithmic_bytes_per_unit(cs.nv, 4, True, True, cs.n_snap)
+    mode, TI, TJ = r32["tuning"]
     launch_ms = r32["tile_ms"] / max(1, r32["tile_n"])
-    achieved = bpu * units_per_launch / (launch_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-            "kernel": "tile2d_kernel<float,7,VISC,RK>", "peak_source": src,
-            "bytes_per_unit": bpu, "units_per_launch": units_per_launch, "launch_ms": launch_ms}
-    tr = _traffic_record("tile2d_f32_ns7_visc")
-    if tr:
-        roof["traffic"] = tr
+    kname = (f"persist_kernel<float,VISC,{TI},{TJ}>" if mode == 1 else f"tile2d_kernel<float,7,VISC,RK,{TI},{TJ}>")
+    roof = roofline(peaks, src, bpu, cs.n_cells * cs.n_snap, mode, launch_ms, kname,
+                    _traffic_record(f"{'persist' if mode == 1 else 'tile2d'}_f32_{TI}x{TJ}_ns_ogrid8"))
     if rank != 0:
         return 0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -325,12 +338,79 @@ def run_ours(args):
                            "steps": args.fp64_steps,
                            "tile_launch_ms": r64["tile_ms"] / max(1, r64["tile_n"])},
             "fp32_over_fp64": value / ws / v64,
+            "tuning": {"driver": "persistent" if mode == 1 else "per-phase launches", "tile": [TI, TJ]},
+            "batched_fp32": batch,
+            "adjoint": adj,
             "kernel_share": {"tile_ms": r32["tile_ms"], "halo_ms": r32["halo_ms"], "step_ms_total": ms32},
             "status": [r32["status"], r64["status"]]}
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_batch(args, dev):
+    """64 independent inviscid pitching O-grids (seeded sizes 32x16..512x256,
+    N_H in 1..4): FP32, all cases advanced together by the library's driver
+    (autotuned); the state (~150 MB) exceeds L2, so no flush is needed."""
+    import numpy as np
+    import torch
+    from paper_1304_7654_gb300 import cases as C
+    from paper_1304_7654_gb300 import hb
+    cases = C.batch_cases()
+    ctx = hb.HBContext(cases, "fp32")
+    U = ctx.new_state(dev)
+    ctx.init_state(U, torch.as_tensor(np.concatenate([C.noise(c) for c in cases]), device=dev), 0.01)
+    mode, TI, TJ = ctx.autotune(U, iters=2)
+    ctx.rk_smooth(U, 3, norms=False)
+    K = max(4, args.steps)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ctx.kernel_stats(0, reset=True)
+    a.record()
+    ctx.rk_smooth(U, K, norms=False)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / K
+    units = sum(c.n_cells * c.n_snap for c in cases) * 4
+    return {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_iteration": ms, "iterations": K,
+            "cases": len(cases), "cells": int(sum(c.n_cells for c in cases)),
+            "cell_snapshots": int(sum(c.n_cells * c.n_snap for c in cases)),
+            "driver": "persistent" if mode == 1 else "per-phase launches", "tile": [TI, TJ],
+            "status": ctx.sync_status()}
+
+
+def adjoint_ratio(dev):
+    """Adjoint/primal time on the 4-block 512x256 laminar N_H=4 case (FP64):
+    hb_adjoint_residual (halo fill, reverse face sweep, gather, ghost
+    transpose) over hb_residual (halo fill and residual)."""
+    import torch
+    from paper_1304_7654_gb300 import cases as C
+    from paper_1304_7654_gb300 import hb
+    cs = C.adjoint_ogrid4()
+    cs.alpha0_deg = 2.0
+    ctx = hb.HBContext(cs, "fp64")
+    U = ctx.new_state(dev)
+    ctx.init_state(U, torch.as_tensor(C.noise(cs), device=dev), 0.01)
+    psi = torch.randn(ctx.size, dtype=torch.float64, device=dev)
+    R = ctx.new_state(dev)
+    r = ctx.new_state(dev)
+
+    def timed(fn, n=5):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    tp = timed(lambda: ctx.residual(U, R))
+    ta = timed(lambda: ctx.adjoint_residual(U, psi, 0.5, r))
+    return {"primal_ms": tp, "adjoint_ms": ta, "ratio": ta / tp,
+            "workload": "adjoint_ogrid4: 4 blocks, 512x256 cells, N_H=4, laminar, FP64"}
 
 
 def _traffic_record(name):
@@ -340,7 +420,8 @@ def _traffic_record(name):
         import hashlib
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)[name]
-        src = open(os.path.join(ROOT, "paper_1304_7654_gb300", "csrc", "hb_kernels.cuh"), "rb").read()
+        src = b"".join(open(os.path.join(ROOT, "paper_1304_7654_gb300", "csrc", n), "rb").read()
+                       for n in rec.get("sources", ["hb_kernels.cuh"]))
         if rec.get("kernel_sha1") != hashlib.sha1(src).hexdigest():
             return None
         return rec["dram_bytes_per_launch"]
@@ -356,14 +437,28 @@ def run_profile(args):
     hbuild.build()
     from paper_1304_7654_gb300 import cases as C
     from paper_1304_7654_gb300 import hb
-    cs = C.ns_ogrid8()
-    ctx = hb.HBContext(cs, args.profile)
-    U = ctx.new_state()
-    ctx.init_state(U, torch.as_tensor(C.noise(cs), device="cuda"), 0.01)
+    if args.profile_batch:
+        import numpy as np
+        cases = C.batch_cases()
+        ctx = hb.HBContext(cases, args.profile)
+        U = ctx.new_state()
+        ctx.init_state(U, torch.as_tensor(np.concatenate([C.noise(c) for c in cases]), device="cuda"), 0.01)
+        cs = cases[0]
+    else:
+        cs = C.ns_ogrid8()
+        ctx = hb.HBContext(cs, args.profile)
+        U = ctx.new_state()
+        ctx.init_state(U, torch.as_tensor(C.noise(cs), device="cuda"), 0.01)
+    if args.tuning:
+        mode, ti, tj = (int(x) for x in args.tuning.split(","))
+        ctx.set_tuning(mode, ti, tj)
     norms = torch.zeros((1, cs.nv), dtype=torch.float64, device="cuda")
     for _ in range(args.warmup + args.steps):
-        ctx.rk_smooth_into(U, 1, norms)
-        ctx.forces_into(U)
+        if args.profile_batch:
+            ctx.rk_smooth_into(U, 1, None)
+        else:
+            ctx.rk_smooth_into(U, 1, norms)
+            ctx.forces_into(U)
     torch.cuda.synchronize()
     st = ctx.sync_status()
     print(json.dumps({"profile": args.profile, "iterations": args.warmup + args.steps, "status": st,
@@ -374,12 +469,16 @@ def run_profile(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--profile", choices=["fp32", "fp64"], default=None)
+    ap.add_argument("--profile-batch", action="store_true")
+    ap.add_argument("--tuning", default=None, help="mode,TI,TJ for --profile (0 per-phase, 1 persistent)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -1032,7 +1032,8 @@ hb_status rk_smooth_impl(hb_ctx* c, T* U, int n_iter, double* norms, cudaStream_
     const bool persist = c->mode == 1 && hbk::persist_available<T>(c->TI, c->TJ);
     // chunks of two or more iterations (or any persistent chunk) replay a
     // captured graph; a persistent chunk runs directly if capture fails
-    bool use_graph = (K >= 2 || persist) && !(persist && c->persist_graph == 0);
+    // (benchmark timing brackets individual launches, so it runs without graphs)
+    bool use_graph = (K >= 2 || persist) && !(persist && c->persist_graph == 0) && !c->timing;
     if (use_graph) {
       auto key = std::make_pair((const void*)U, K * 8 + c->mode);
       auto it = c->graphs.find(key);
