@@ -98,7 +98,8 @@ typedef struct {
  * p_inf = 1/gamma, |u_inf| = mach, mu = mach/reynolds (constant),
  * heat conductivity mu/((gamma-1) prandtl), reference length 1. */
 typedef struct {
-  int dim;                    /* 2 or 3 (3D requires viscous or inviscid boxes) */
+  int dim;                    /* 2 or 3; 3D runs one launch per phase with 8x8x4 tiles and has no
+                                 force integration or adjoint (HB_ERR_UNSUPPORTED) */
   int n_harm;                 /* N_H, 0 .. HB_MAX_HARMONICS */
   double mach, reynolds, prandtl, gamma;
   double alpha0_deg;          /* mean incidence of the freestream */

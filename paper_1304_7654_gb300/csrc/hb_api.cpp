@@ -529,6 +529,17 @@ hb_status rebuild_tiles(hb_ctx* c, int TI, int TJ) {
     ch.tile0 = (int)tiles.size();
     for (int b = 0; b < ch.nblocks; ++b) {
       const BlockDev& B = c->blocks[ch.block0 + b];
+      if (c->dim == 3) {   // fixed 8 x 8 x 4 tiles
+        for (int k = 0; k < B.n[2]; k += 4)
+          for (int j = 0; j < B.n[1]; j += 8)
+            for (int i = 0; i < B.n[0]; i += 8) {
+              const long long cells = (long long)std::min(8, B.n[0] - i) * std::min(8, B.n[1] - j) *
+                                      std::min(4, B.n[2] - k);
+              cost.push_back({-(cells * ch.ns), (int)tiles.size()});
+              tiles.push_back(make_int4(ch.block0 + b, i, j, k));
+            }
+        continue;
+      }
       for (int j = 0; j < B.n[1]; j += TJ)
         for (int i = 0; i < B.n[0]; i += TI) {
           const long long cells = (long long)std::min(TI, B.n[0] - i) * std::min(TJ, B.n[1] - j);
@@ -628,7 +639,7 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
   ctx->prec = d0.prec;
   ctx->viscous = d0.viscous;
   ctx->tsize = (d0.prec == HB_FP32) ? sizeof(float) : sizeof(double);
-  if (d0.dim != 2) return bad(HB_ERR_UNSUPPORTED, "only dim = 2 is built in this library version");
+  if (d0.dim != 2 && d0.dim != 3) return bad(HB_ERR_INVALID_ARG, "dim must be 2 or 3");
   if (d0.prec != HB_FP32 && d0.prec != HB_FP64) return bad(HB_ERR_INVALID_ARG, "bad precision");
   int64_t off = 0, goff = 0, noff = 0;
   for (int c = 0; c < n; ++c) {
@@ -654,15 +665,15 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
     ctx->n_bodies = std::max(ctx->n_bodies, d.n_bodies);
     for (int b = 0; b < d.n_blocks; ++b) {
       const hb_block_desc& bd = d.blocks[b];
-      if (bd.ni < 1 || bd.nj < 1 || bd.nk != 1 || !bd.nodes)
+      if (bd.ni < 1 || bd.nj < 1 || bd.nk < 1 || (d.dim == 2 && bd.nk != 1) || !bd.nodes)
         return bad(HB_ERR_INVALID_ARG, "bad block " + std::to_string(b));
       BlockDev B;
       memset(&B, 0, sizeof(B));
-      B.n[0] = bd.ni; B.n[1] = bd.nj; B.n[2] = 1;
-      B.gk = 0;
+      B.n[0] = bd.ni; B.n[1] = bd.nj; B.n[2] = bd.nk;
+      B.gk = (d.dim == 3) ? 2 : 0;
       B.P[0] = round_up(bd.ni + 4, 8);
       B.P[1] = bd.nj + 4;
-      B.P[2] = 1;
+      B.P[2] = (d.dim == 3) ? bd.nk + 4 : 1;
       B.plane = (int64_t)B.P[0] * B.P[1] * B.P[2];
       B.plane = (B.plane + 31) / 32 * 32;
       B.off = off;
@@ -671,7 +682,7 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
       B.cs = c;
       off += B.plane * ch.ns * ch.nv;
       goff += B.plane;
-      const int64_t cells = (int64_t)bd.ni * bd.nj;
+      const int64_t cells = (int64_t)bd.ni * bd.nj * bd.nk;
       noff += cells * ch.ns * ch.nv;
       ch.cells += cells;
       ctx->blocks.push_back(B);
@@ -698,10 +709,12 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
       const BlockDev& B = ctx->blocks[ch.block0 + b];
       // interior cells must be right-handed; ghost cells reflected through a
       // sharp corner may be inverted but must not be degenerate
+      const int kg = B.gk;
+      for (int k = -kg; k < B.n[2] + kg; ++k)
       for (int j = -2; j < B.n[1] + 2; ++j)
         for (int i = -2; i < B.n[0] + 2; ++i) {
-          const double v = G[(size_t)hbk::G_VOL * ctx->geo_cells + B.goff + pcell(B, i, j, 0)];
-          const bool in = i >= 0 && i < B.n[0] && j >= 0 && j < B.n[1];
+          const double v = G[(size_t)hbk::G_VOL * ctx->geo_cells + B.goff + pcell(B, i, j, k)];
+          const bool in = i >= 0 && i < B.n[0] && j >= 0 && j < B.n[1] && k >= 0 && k < B.n[2];
           if (in ? !(v > 0.0) : !(v != 0.0 && std::isfinite(v)))
             return bad(HB_ERR_INVALID_ARG, in ? "non-positive interior cell volume (left-handed block)"
                                               : "degenerate ghost cell (zero volume)");
@@ -783,9 +796,9 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     key += "_sm" + std::to_string(sms);
     ctx->tune_key = key.substr(0, 500);
-    int m = (ctx->cases.size() > 1 && ctx->prec == HB_FP32) ? 1 : 0, a = 32, b = 8;
+    int m = (ctx->cases.size() > 1 && ctx->prec == HB_FP32 && ctx->dim == 2) ? 1 : 0, a = 32, b = 8;
     int mm, aa, bb;
-    if (tune_lookup(ctx->tune_key, &mm, &aa, &bb)) { m = mm; a = aa; b = bb; }
+    if (ctx->dim == 2 && tune_lookup(ctx->tune_key, &mm, &aa, &bb)) { m = mm; a = aa; b = bb; }
     ctx->mode = m;
     hb_status st = rebuild_tiles(ctx, a, b);
     if (st != HB_OK) return bad(st, ctx->err);
@@ -871,7 +884,8 @@ hb_status halos(hb_ctx* c, T* U, cudaStream_t s) {
     p.nbc = c->nbc[pass];
     if ((int64_t)(p.ncopy + p.nbc) == 0) continue;
     TimedScope ts(c, 1, s);
-    HB_CUDA(c, hbk::launch_halo<T>(p, s));
+    if (c->dim == 3) HB_CUDA(c, hbk::launch_halo3d<T>(p, s));
+    else HB_CUDA(c, hbk::launch_halo<T>(p, s));
   }
   return HB_OK;
 }
@@ -898,7 +912,8 @@ hb_status stage_all(hb_ctx* c, hbk::StageParams<T> p, int mode, cudaStream_t s) 
     double* part = p.partials;
     if (part) p.partials = part + (size_t)8 * ch.tile0;
     TimedScope ts(c, 0, s);
-    HB_CUDA(c, hbk::launch_stage<T>(p, ch.ns, c->viscous, mode, s));
+    if (c->dim == 3) HB_CUDA(c, hbk::launch_stage3d<T>(p, ch.ns, c->viscous, mode, s));
+    else HB_CUDA(c, hbk::launch_stage<T>(p, ch.ns, c->viscous, mode, s));
     p.partials = part;
   }
   return HB_OK;
@@ -1157,6 +1172,11 @@ hb_status forces_filled(hb_ctx* c, const T* W, double* coef, double* J, cudaStre
 template <typename T>
 hb_status init_impl(hb_ctx* c, T* U, const double* noise, double amp, cudaStream_t s) {
   c->n_launch += (int64_t)c->blocks.size();
+  if (c->dim == 3) {
+    HB_CUDA(c, hbk::launch_init3d<T>((const CaseDev<T>*)c->d_cases, c->d_blocks, (int)c->blocks.size(),
+                                     geo_of<T>(c), U, noise, amp, s));
+    return HB_OK;
+  }
   HB_CUDA(c, hbk::launch_init<T>((const CaseDev<T>*)c->d_cases, c->d_blocks, (int)c->blocks.size(),
                                  geo_of<T>(c), U, noise, amp, c->interior_values, nullptr, s));
   return HB_OK;
@@ -1227,6 +1247,8 @@ hb_status hb_rk_smooth(hb_ctx* ctx, void* U, int n_iter, double* norms, void* st
 hb_status hb_forces(hb_ctx* ctx, const void* U, double* coef, double* J, void* stream) {
   if (!ctx || !U) return fail(ctx, HB_ERR_INVALID_ARG, "null argument");
   if (ctx->cases.size() != 1) return fail(ctx, HB_ERR_UNSUPPORTED, "hb_forces needs a single-case context");
+  if (ctx->dim == 3 && ctx->cases[0].d.n_bodies > 0)
+    return fail(ctx, HB_ERR_UNSUPPORTED, "3D force integration is not built");
   cudaStream_t s = (cudaStream_t)stream;
   return ctx->prec == HB_FP32 ? forces_impl<float>(ctx, (const float*)U, coef, J, s)
                               : forces_impl<double>(ctx, (const double*)U, coef, J, s);
@@ -1280,6 +1302,7 @@ hb_status hb_adjoint_residual(hb_ctx* ctx, const void* U, const void* psi, doubl
 
 hb_status hb_autotune(hb_ctx* ctx, const void* U, int iters, void* stream) {
   if (!ctx || !U || iters < 1) return fail(ctx, HB_ERR_INVALID_ARG, "bad argument");
+  if (ctx->dim == 3) return HB_OK;   // one 3D tile shape and driver: nothing to choose
   cudaStream_t s = (cudaStream_t)stream;
   return ctx->prec == HB_FP32 ? autotune_impl<float>(ctx, (const float*)U, iters, s)
                               : autotune_impl<double>(ctx, (const double*)U, iters, s);
@@ -1287,6 +1310,7 @@ hb_status hb_autotune(hb_ctx* ctx, const void* U, int iters, void* stream) {
 
 hb_status hb_set_tuning(hb_ctx* ctx, int mode, int TI, int TJ) {
   if (!ctx || mode < 0 || mode > 1) return fail(ctx, HB_ERR_INVALID_ARG, "bad tuning");
+  if (ctx->dim == 3) return fail(ctx, HB_ERR_UNSUPPORTED, "3D contexts use fixed 8x8x4 tiles, one launch per phase");
   const bool ok = (TI == 32 && TJ == 8) || (TI == 32 && TJ == 4) || (TI == 16 && TJ == 8);
   if (!ok) return fail(ctx, HB_ERR_UNSUPPORTED, "tile shape not built");
   const bool pok = ctx->prec == HB_FP32 ? hbk::persist_available<float>(TI, TJ)

@@ -151,6 +151,13 @@ template <typename T>
 cudaError_t stage_smem_bytes(int TI, int TJ, size_t* bytes);
 
 template <typename T>
+cudaError_t launch_stage3d(const StageParams<T>& p, int ns, int viscous, int mode, cudaStream_t s);
+template <typename T>
+cudaError_t launch_halo3d(const HaloParams<T>& p, cudaStream_t s);
+template <typename T>
+cudaError_t launch_init3d(const CaseDev<T>* cases, const BlockDev* blocks, int nblocks, Geo<T> g, T* U,
+                          const double* noise, double amp, cudaStream_t s);
+template <typename T>
 cudaError_t launch_persist(const PersistParams<T>& p, int viscous, int TI, int TJ, cudaStream_t s,
                            int* grid_out);
 template <typename T>

@@ -1,0 +1,401 @@
+// 3D tile kernel of the HB residual path: the same method and readings as the
+// 2D kernel (hb_kernels.cuh) with five conservative variables, three face
+// directions and the full 3x3 Stokes stress.
+//
+// One CTA owns an 8 x 8 x 4 tile of one block and loops over all snapshots;
+// per snapshot it stages primitives (rho, u, v, w, p) and T of the tile plus a
+// 2-cell halo in shared memory, computes Green-Gauss gradients of (u, v, w, T)
+// on the 1-cell ring, then every face of the tile once (MUSCL + van Albada,
+// Roe, viscous), and keeps the flux balance of each own cell in shared
+// memory; the HB source and the RK update run in the epilogue.  Face vectors
+// and centre differences come through the read-only data cache.
+#pragma once
+
+#include "hb_kernels.cuh"
+
+namespace hbk {
+
+constexpr int T3I = 8, T3J = 8, T3K = 4;
+
+template <typename T>
+__device__ __forceinline__ void roe3d(const T* WL, const T* WR, T Sx, T Sy, T Sz, T vgn, T gm1, T gg1,
+                                      T ig1, int efix, T efrac, T* F) {
+  const T A2 = Sx * Sx + Sy * Sy + Sz * Sz;
+  const T iA = Ar<T>::rsq(A2);
+  const T A = A2 * iA;
+  const T nx = Sx * iA, ny = Sy * iA, nz = Sz * iA;
+  const T irL = Ar<T>::rcp(WL[0]), irR = Ar<T>::rcp(WR[0]);
+  const T qL = WL[1] * nx + WL[2] * ny + WL[3] * nz;
+  const T qR = WR[1] * nx + WR[2] * ny + WR[3] * nz;
+  const T kL = T(0.5) * (WL[1] * WL[1] + WL[2] * WL[2] + WL[3] * WL[3]);
+  const T kR = T(0.5) * (WR[1] * WR[1] + WR[2] * WR[2] + WR[3] * WR[3]);
+  const T HL = gg1 * WL[4] * irL + kL;
+  const T HR = gg1 * WR[4] * irR + kR;
+  const T rr = WR[0] * irL;
+  const T r = rr * Ar<T>::rsq(rr);
+  const T rt = r * WL[0];
+  const T inv1r = Ar<T>::rcp(T(1) + r);
+  const T ut = (WL[1] + r * WR[1]) * inv1r;
+  const T vt = (WL[2] + r * WR[2]) * inv1r;
+  const T wt = (WL[3] + r * WR[3]) * inv1r;
+  const T Ht = (HL + r * HR) * inv1r;
+  const T kt = T(0.5) * (ut * ut + vt * vt + wt * wt);
+  const T ct2 = gm1 * (Ht - kt);
+  const T ict = Ar<T>::rsq(ct2);
+  const T ct = ct2 * ict;
+  const T ict2 = ict * ict;
+  const T qt = ut * nx + vt * ny + wt * nz;
+  const T qtr = qt - vgn;
+  T l1 = fabs(qtr - ct), l2 = fabs(qtr), l3 = fabs(qtr + ct);
+  if (efix) {
+    const T del = efrac * ct;
+    if (l1 < del) l1 = (l1 * l1 + del * del) * (T(0.5) * Ar<T>::rcp(del));
+    if (l3 < del) l3 = (l3 * l3 + del * del) * (T(0.5) * Ar<T>::rcp(del));
+  }
+  const T dp = WR[4] - WL[4], drho = WR[0] - WL[0], dq = qR - qL;
+  const T a1 = T(0.5) * (dp - rt * ct * dq) * ict2;
+  const T a3 = T(0.5) * (dp + rt * ct * dq) * ict2;
+  const T a2 = drho - dp * ict2;
+  const T dux = (WR[1] - WL[1]) - dq * nx;
+  const T duy = (WR[2] - WL[2]) - dq * ny;
+  const T duz = (WR[3] - WL[3]) - dq * nz;
+  const T udu = ut * dux + vt * duy + wt * duz;
+  const T w1 = l1 * a1, w3 = l3 * a3;
+  const T D0 = w1 + l2 * a2 + w3;
+  const T D1 = w1 * (ut - ct * nx) + l2 * (a2 * ut + rt * dux) + w3 * (ut + ct * nx);
+  const T D2 = w1 * (vt - ct * ny) + l2 * (a2 * vt + rt * duy) + w3 * (vt + ct * ny);
+  const T D3 = w1 * (wt - ct * nz) + l2 * (a2 * wt + rt * duz) + w3 * (wt + ct * nz);
+  const T D4 = w1 * (Ht - ct * qt) + l2 * (a2 * kt + rt * udu) + w3 * (Ht + ct * qt);
+  const T qLr = qL - vgn, qRr = qR - vgn;
+  const T EL = WL[4] * ig1 + WL[0] * kL, ER = WR[4] * ig1 + WR[0] * kR;
+  const T hA = T(0.5) * A;
+  F[0] = hA * (WL[0] * qLr + WR[0] * qRr - D0);
+  F[1] = hA * (WL[0] * WL[1] * qLr + WL[4] * nx + WR[0] * WR[1] * qRr + WR[4] * nx - D1);
+  F[2] = hA * (WL[0] * WL[2] * qLr + WL[4] * ny + WR[0] * WR[2] * qRr + WR[4] * ny - D2);
+  F[3] = hA * (WL[0] * WL[3] * qLr + WL[4] * nz + WR[0] * WR[3] * qRr + WR[4] * nz - D3);
+  F[4] = hA * (EL * qLr + WL[4] * qL + ER * qRr + WR[4] * qR - D4);
+}
+
+// viscous flux through S from gradients gL, gR [4 quantities][3] (u, v, w, T),
+// cell values phiL, phiR (u, v, w, T) and the centre difference t = x_R - x_L
+template <typename T>
+__device__ __forceinline__ void visc3d(const T* gL, const T* gR, const T* pL, const T* pR, T tx, T ty, T tz,
+                                       T Sx, T Sy, T Sz, T mu, T kap, T* Fv) {
+  const T il = Ar<T>::rsq(tx * tx + ty * ty + tz * tz);
+  const T e[3] = {tx * il, ty * il, tz * il};
+  T g[12];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    T b[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) b[a] = T(0.5) * (gL[3 * q + a] + gR[3 * q + a]);
+    const T corr = (pR[q] - pL[q]) * il - (b[0] * e[0] + b[1] * e[1] + b[2] * e[2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[3 * q + a] = b[a] + corr * e[a];
+  }
+  const T div = g[0] + g[4] + g[8];
+  const T S[3] = {Sx, Sy, Sz};
+  T f[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T tau = mu * (g[3 * a + c] + g[3 * c + a]);
+      if (a == c) tau -= T(2.0 / 3.0) * mu * div;
+      s += tau * S[c];
+    }
+    f[a] = s;
+  }
+  Fv[0] = T(0);
+  Fv[1] = f[0];
+  Fv[2] = f[1];
+  Fv[3] = f[2];
+  Fv[4] = T(0.5) * ((pL[0] + pR[0]) * f[0] + (pL[1] + pR[1]) * f[1] + (pL[2] + pR[2]) * f[2]) +
+          kap * (g[9] * Sx + g[10] * Sy + g[11] * Sz);
+}
+
+__host__ __device__ constexpr size_t tile3d_smem_elems(int NS) {
+  return (size_t)7 * (T3I + 4) * (T3J + 4) * (T3K + 4) + (size_t)12 * (T3I + 2) * (T3J + 2) * (T3K + 2) +
+         (size_t)5 * ((T3I + 1) * T3J * T3K + T3I * (T3J + 1) * T3K + T3I * T3J * (T3K + 1)) +
+         (size_t)NS * 5 * T3I * T3J * T3K + (size_t)NS * NS;
+}
+
+template <typename T, int NS, bool VISC, int MODE>
+__device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
+  constexpr int NV = 5;
+  constexpr int TI = T3I, TJ = T3J, TK = T3K, NT = TI * TJ * TK;
+  constexpr int RI = TI + 4, RJ = TJ + 4, RK = TK + 4, NR = RI * RJ * RK;
+  constexpr int GI = TI + 2, GJ = TJ + 2, GK = TK + 2, NG = GI * GJ * GK;
+  constexpr int NFI = (TI + 1) * TJ * TK, NFJ = TI * (TJ + 1) * TK, NFK = TI * TJ * (TK + 1);
+  constexpr int NF = NFI + NFJ + NFK;
+  const int4 tl = P.tiles[t];
+  const BlockDev B = P.blocks[tl.x];
+  const CaseDev<T>* C = P.cases + B.cs;
+  const int i0 = tl.y, j0 = tl.z, k0 = tl.w;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int P0 = B.P[0], P1 = B.P[1];
+  const int n0 = B.n[0], n1 = B.n[1], n2 = B.n[2];
+  const int64_t sJ = P0, sK = (int64_t)P0 * P1;
+
+  T* sW = sm;              // [5][NR] rho, u, v, w, p
+  T* sT = sW + 5 * NR;     // [NR]
+  T* sIV = sT + NR;        // [NR]
+  T* sG = sIV + NR;        // [12][NG]
+  T* sF = sG + 12 * NG;    // [NV][NF]
+  T* sAcc = sF + NV * NF;  // [NS][NV][NT]
+  T* sD = sAcc + NS * NV * NT;
+
+  const T gam = C->gamma, gm1 = C->gamma - T(1), eps = C->eps, efrac = C->ent_frac;
+  const T gg1 = gam / gm1, ig1 = T(1) / gm1;
+  const T mu = C->mu, kap = C->kappa, omega = C->omega;
+  const int efix = C->entropy_fix;
+  const bool moving = C->motion != 0;
+  const T* gS[3][3];
+  const T* gDc[3][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { gS[d][a] = P.g.q[G_S + 3 * d + a] + B.goff; gDc[d][a] = P.g.q[G_DC + 3 * d + a] + B.goff; }
+
+  auto rcell = [&](int ri, int rj, int rk) { return (rk * RJ + rj) * RI + ri; };
+  auto pcell = [&](int i, int j, int k) -> int64_t { return (int64_t)(k + 2) * sK + (int64_t)(j + 2) * sJ + (i + 2); };
+  auto inpad = [&](int i, int j, int k) { return i <= n0 + 1 && j <= n1 + 1 && k <= n2 + 1; };
+
+  for (int r = tid; r < NR; r += nt) {
+    const int ri = r % RI, rj = (r / RI) % RJ, rk = r / (RI * RJ);
+    const int i = i0 - 2 + ri, j = j0 - 2 + rj, k = k0 - 2 + rk;
+    sIV[r] = inpad(i, j, k) ? Ar<T>::rcp(P.g.q[G_VOL][B.goff + pcell(i, j, k)]) : T(1);
+  }
+  for (int e = tid; e < NS * NS; e += nt) sD[e] = C->D[e];
+
+  const int ti = tid % TI, tj = (tid / TI) % TJ, tk = tid / (TI * TJ);
+  const int ci = i0 + ti, cj = j0 + tj, ck = k0 + tk;
+  const bool own = (tid < NT) && ci < n0 && cj < n1 && ck < n2;
+  const int rown = rcell(ti + 2, tj + 2, tk + 2);
+  const int64_t cown = pcell(ci, cj, ck);
+
+  for (int n = 0; n < NS; ++n) {
+    const Fr<T> f = frame_at(C, n);
+    __syncthreads();
+    for (int r = tid; r < NR; r += nt) {
+      const int ri = r % RI, rj = (r / RI) % RJ, rk = r / (RI * RJ);
+      const int i = i0 - 2 + ri, j = j0 - 2 + rj, k = k0 - 2 + rk;
+      T w[5] = {T(1), T(0), T(0), T(0), T(1)}, tt = gam;
+      if (inpad(i, j, k)) {
+        const T* u = P.Uprev + B.off + (int64_t)n * NV * B.plane + pcell(i, j, k);
+        const T rho = u[0], ir = Ar<T>::rcp(rho);
+        w[0] = rho;
+        w[1] = u[B.plane] * ir;
+        w[2] = u[2 * B.plane] * ir;
+        w[3] = u[3 * B.plane] * ir;
+        w[4] = gm1 * (u[4 * B.plane] - T(0.5) * rho * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]));
+        tt = gam * w[4] * ir;
+      }
+#pragma unroll
+      for (int q = 0; q < 5; ++q) sW[q * NR + r] = w[q];
+      sT[r] = tt;
+    }
+    __syncthreads();
+    if (VISC) {
+      for (int gq = tid; gq < NG; gq += nt) {
+        const int gi = gq % GI, gj = (gq / GI) % GJ, gk = gq / (GI * GJ);
+        const int r = rcell(gi + 1, gj + 1, gk + 1);
+        const int i = i0 - 1 + gi, j = j0 - 1 + gj, k = k0 - 1 + gk;
+        T g[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) g[q] = T(0);
+        // ring cells beyond index n are never L or R of a computed face; their
+        // high faces would lie outside the padded block
+        if (i > n0 || j > n1 || k > n2) {
+#pragma unroll
+          for (int q = 0; q < 12; ++q) sG[q * NG + gq] = T(0);
+          continue;
+        }
+        const T pc[4] = {sW[NR + r], sW[2 * NR + r], sW[3 * NR + r], sT[r]};
+        const int rs[3] = {1, RI, RI * RJ};
+        const int64_t cs[3] = {1, sJ, sK};
+        const int64_t c = pcell(i, j, k);
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int side = 0; side < 2; ++side) {
+            const int o = side ? r + rs[d] : r - rs[d];
+            const int64_t fc = side ? c + cs[d] : c;      // owner of the face
+            const T s0 = __ldg(gS[d][0] + fc), s1 = __ldg(gS[d][1] + fc), s2 = __ldg(gS[d][2] + fc);
+            T sx, sy;
+            rotv(f, s0, s1, sx, sy);
+            const T sg = side ? T(0.5) : T(-0.5);
+            const T sv[3] = {sg * sx, sg * sy, sg * s2};
+            const T dphi[4] = {sW[NR + o] - pc[0], sW[2 * NR + o] - pc[1], sW[3 * NR + o] - pc[2], sT[o] - pc[3]};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+              for (int a = 0; a < 3; ++a) g[3 * q + a] += dphi[q] * sv[a];
+          }
+        const T iv = sIV[r];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) sG[q * NG + gq] = g[q] * iv;
+      }
+      __syncthreads();
+    }
+    for (int fq = tid; fq < NF; fq += nt) {
+      int d, fi, fj, fk;
+      if (fq < NFI) { d = 0; fi = fq % (TI + 1); fj = (fq / (TI + 1)) % TJ; fk = fq / ((TI + 1) * TJ); }
+      else if (fq < NFI + NFJ) { const int q2 = fq - NFI; d = 1; fi = q2 % TI; fj = (q2 / TI) % (TJ + 1); fk = q2 / (TI * (TJ + 1)); }
+      else { const int q3 = fq - NFI - NFJ; d = 2; fi = q3 % TI; fj = (q3 / TI) % TJ; fk = q3 / (TI * TJ); }
+      // the face is the low face of cell R = (i0+fi, j0+fj, k0+fk) along d
+      const int Ri = i0 + fi, Rj = j0 + fj, Rk = k0 + fk;
+      if (Ri > n0 - (d != 0) || Rj > n1 - (d != 1) || Rk > n2 - (d != 2)) continue;
+      const int st = (d == 0) ? 1 : (d == 1 ? RI : RI * RJ);
+      const int rR = rcell(fi + 2, fj + 2, fk + 2);
+      const int rL = rR - st;
+      T WL[5], WR[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        const T a = sW[q * NR + rL - st], b = sW[q * NR + rL], c = sW[q * NR + rR], dd = sW[q * NR + rR + st];
+        WL[q] = b + T(0.5) * van_albada(b - a, c - b, eps);
+        WR[q] = c - T(0.5) * van_albada(c - b, dd - c, eps);
+      }
+      const int64_t gR = pcell(Ri, Rj, Rk);
+      T sx, sy;
+      rotv(f, __ldg(gS[d][0] + gR), __ldg(gS[d][1] + gR), sx, sy);
+      const T sz = __ldg(gS[d][2] + gR);
+      T vgn = T(0);
+      if (moving) {
+        T xf, yf;
+        rotp(f, __ldg(P.g.q[G_XF + 3 * d] + B.goff + gR), __ldg(P.g.q[G_XF + 3 * d + 1] + B.goff + gR), xf, yf);
+        const T vgx = -f.thd * (yf - f.py), vgy = f.thd * (xf - f.px);
+        vgn = (vgx * sx + vgy * sy) * Ar<T>::rsq(sx * sx + sy * sy + sz * sz);
+      }
+      T F[5];
+      roe3d(WL, WR, sx, sy, sz, vgn, gm1, gg1, ig1, efix, efrac, F);
+      if (VISC) {
+        // ring index of L and R
+        const int gRi = ((fk + 1) * GJ + (fj + 1)) * GI + (fi + 1);
+        const int gs = (d == 0) ? 1 : (d == 1 ? GI : GI * GJ);
+        const int gLi = gRi - gs;
+        T gl[12], gr[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) { gl[q] = sG[q * NG + gLi]; gr[q] = sG[q * NG + gRi]; }
+        T tx, ty;
+        rotv(f, __ldg(gDc[d][0] + gR), __ldg(gDc[d][1] + gR), tx, ty);
+        const T tz = __ldg(gDc[d][2] + gR);
+        const T pL[4] = {sW[NR + rL], sW[2 * NR + rL], sW[3 * NR + rL], sT[rL]};
+        const T pR[4] = {sW[NR + rR], sW[2 * NR + rR], sW[3 * NR + rR], sT[rR]};
+        T Fv[5];
+        visc3d(gl, gr, pL, pR, tx, ty, tz, sx, sy, sz, mu, kap, Fv);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) F[q] -= Fv[q];
+      }
+#pragma unroll
+      for (int q = 0; q < 5; ++q) sF[q * NF + fq] = F[q];
+    }
+    __syncthreads();
+    if (own) {
+      const int fi0 = (tk * TJ + tj) * (TI + 1) + ti;
+      const int fj0 = NFI + (tk * (TJ + 1) + tj) * TI + ti;
+      const int fk0 = NFI + NFJ + (tk * TJ + tj) * TI + ti;
+#pragma unroll
+      for (int q = 0; q < NV; ++q)
+        sAcc[(n * NV + q) * NT + tid] = (sF[q * NF + fi0 + 1] - sF[q * NF + fi0]) +
+                                        (sF[q * NF + fj0 + TI] - sF[q * NF + fj0]) +
+                                        (sF[q * NF + fk0 + TI * TJ] - sF[q * NF + fk0]);
+    }
+  }
+
+  T tacc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) tacc[q] = T(0);
+  double nacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (own) {
+    const T V = P.g.q[G_VOL][B.goff + cown];
+    const T vw = V * omega;
+    const T iV = sIV[rown];
+    T uu[NS][NV];
+#pragma unroll
+    for (int m = 0; m < NS; ++m)
+#pragma unroll
+      for (int q = 0; q < NV; ++q) uu[m][q] = P.Uprev[B.off + ((int64_t)m * NV + q) * B.plane + cown];
+    T Sb[3][3], m2[3], mg[3];
+    const int64_t cs[3] = {1, sJ, sK};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Sb[d][a] = T(0.5) * (__ldg(gS[d][a] + cown) + __ldg(gS[d][a] + cown + cs[d]));
+      m2[d] = Sb[d][0] * Sb[d][0] + Sb[d][1] * Sb[d][1] + Sb[d][2] * Sb[d][2];
+      mg[d] = m2[d] * Ar<T>::rsq(m2[d]);
+    }
+    for (int n = 0; n < NS; ++n) {
+      T Rn[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        T h = T(0);
+#pragma unroll
+        for (int m = 0; m < NS; ++m) h += sD[n * NS + m] * uu[m][q];
+        Rn[q] = sAcc[(n * NV + q) * NT + tid] + vw * h;
+      }
+      const int64_t base = B.off + (int64_t)n * NV * B.plane + cown;
+      if (MODE == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) P.R[base + q * B.plane] = Rn[q];
+      } else {
+        T u0[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) u0[q] = P.U0[base + q * B.plane];
+        const Fr<T> f = frame_at(C, n);
+        const T rho = u0[0], irho = Ar<T>::rcp(rho);
+        const T uv = u0[1] * irho, vv = u0[2] * irho, wv = u0[3] * irho;
+        const T pp = gm1 * (u0[4] - T(0.5) * rho * (uv * uv + vv * vv + wv * wv));
+        const T c2 = gam * pp * irho;
+        const T cs_ = c2 * Ar<T>::rsq(c2);
+        T ur[3] = {uv, vv, wv};
+        if (moving) {
+          T xc, yc;
+          rotp(f, P.g.q[G_XC][B.goff + cown], P.g.q[G_XC + 1][B.goff + cown], xc, yc);
+          ur[0] -= -f.thd * (yc - f.py);
+          ur[1] -= f.thd * (xc - f.px);
+        }
+        T lam = T(0);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          T ax, ay;
+          rotv(f, Sb[d][0], Sb[d][1], ax, ay);
+          lam += fabs(ur[0] * ax + ur[1] * ay + ur[2] * Sb[d][2]) + cs_ * mg[d];
+        }
+        if (VISC) {
+          const T cv = (gam / C->prandtl > T(4.0 / 3.0)) ? gam / C->prandtl : T(4.0 / 3.0);
+          lam += T(4) * cv * (mu * irho) * (m2[0] + m2[1] + m2[2]) * iV;
+        }
+        lam += omega * T(C->nh) * V;
+        const T fac = P.alpha * C->cfl * Ar<T>::rcp(lam);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) P.Unext[base + q * B.plane] = u0[q] - fac * Rn[q];
+        if (P.partials) {
+#pragma unroll
+          for (int q = 0; q < NV; ++q) {
+            const T x = Rn[q] * iV;
+            tacc[q] += x * x;
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) nacc[q] = (double)tacc[q];
+  if (MODE == 1 && P.partials) {
+    __syncthreads();
+    double* scratch = reinterpret_cast<double*>(sm);
+    block_sum8(nacc, NV, scratch);
+    if (threadIdx.x == 0)
+      for (int q = 0; q < NV; ++q) P.partials[(int64_t)t * 8 + q] = nacc[q];
+  }
+}
+
+template <typename T, int NS, bool VISC, int MODE>
+__global__ void __launch_bounds__(T3I * T3J * T3K, sizeof(T) == 4 ? 2 : 1) tile3d_kernel(StageParams<T> P) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  tile3d<T, NS, VISC, MODE>(P, blockIdx.x, reinterpret_cast<T*>(smraw));
+}
+
+}  // namespace hbk

@@ -1,0 +1,4 @@
+// F64 instantiation of the 3D tile, halo and init kernels.
+#include "hb_kernels3d.cuh"
+#define HB_T double
+#include "hb_launch3d.inc"
