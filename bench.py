@@ -263,6 +263,7 @@ def run_ours(args):
     r64 = run_prec("fp64", args.fp64_steps, 2, tune=False)
     batch = run_batch(args, dev) if not args.no_batch else None
     adj = adjoint_ratio(dev) if not args.no_adjoint else None
+    box = run_box3d(args, dev) if not args.no_batch else None
 
     # e2e: host buffers in pinned memory, H2D of the state and D2H of the
     # step's results (norms, force coefficients, J) inside the timed region
@@ -341,6 +342,7 @@ def run_ours(args):
             "tuning": {"driver": "persistent" if mode == 1 else "per-phase launches", "tile": [TI, TJ]},
             "batched_fp32": batch,
             "adjoint": adj,
+            "box3d_fp32": box,
             "kernel_share": {"tile_ms": r32["tile_ms"], "halo_ms": r32["halo_ms"], "step_ms_total": ms32},
             "status": [r32["status"], r64["status"]]}
     if not args.no_cpu_baseline and ws == 1:
@@ -377,6 +379,49 @@ def run_batch(args, dev):
             "cases": len(cases), "cells": int(sum(c.n_cells for c in cases)),
             "cell_snapshots": int(sum(c.n_cells * c.n_snap for c in cases)),
             "driver": "persistent" if mode == 1 else "per-phase launches", "tile": [TI, TJ],
+            "status": ctx.sync_status()}
+
+
+def run_box3d(args, dev):
+    """3D laminar HB NS box, 256x128x64 cells, N_H = 2, FP32 (state ~240 MB,
+    larger than L2): per-kernel CUDA-event times and achieved algorithmic
+    GB/s of the tile kernel (one RK stage per launch) and the halo kernel."""
+    import torch
+    from paper_1304_7654_gb300 import cases as C
+    from paper_1304_7654_gb300 import hb
+    cs = C.box3d()
+    ctx = hb.HBContext(cs, "fp32")
+    U = ctx.new_state(dev)
+    ctx.init_state(U, torch.as_tensor(C.noise(cs), device=dev), 0.01)
+    ctx.rk_smooth(U, 2, norms=False)
+    steps = max(3, min(args.steps, 20))
+    torch.cuda.synchronize()
+    ctx.kernel_stats(0, reset=True)
+    ctx.set_timing(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        ctx.rk_smooth(U, 1, norms=False)
+    b.record()
+    torch.cuda.synchronize()
+    tile_ms, tile_n = ctx.kernel_stats(0)
+    halo_ms, halo_n = ctx.kernel_stats(1)
+    ctx.set_timing(False)
+    ms = a.elapsed_time(b) / steps
+    cells_snaps = cs.n_cells * cs.n_snap
+    nv, s = 5, 4
+    tile_bytes = ((2 + 3 + 3 + 3) / 4.0 * nv * s + (1 + 9 + 9) * s / cs.n_snap) * cells_snaps
+    ghosts = sum((b_.n[0] + 4) * (b_.n[1] + 4) * (b_.n[2] + 4) - b_.n[0] * b_.n[1] * b_.n[2] for b_ in cs.blocks)
+    halo_bytes = 2 * ghosts * nv * s * cs.n_snap / 3.0            # per pass, three passes per stage
+    tl = tile_ms / max(1, tile_n)
+    hl = halo_ms / max(1, halo_n)
+    peaks, _ = _peaks()
+    return {"value": cells_snaps * 4 / (ms * 1e-3), "unit": UNIT, "ms_per_iteration": ms,
+            "workload": "ns_box3d: 256x128x64 cells, N_H=2, laminar, gust farfield, FP32",
+            "tile_kernel": {"launch_ms": tl, "algorithmic_GBs": tile_bytes / (tl * 1e-3) / 1e9,
+                            "frac_of_measured_hbm": tile_bytes / (tl * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+            "halo_kernel": {"launch_ms": hl, "algorithmic_GBs": halo_bytes / (hl * 1e-3) / 1e9,
+                            "frac_of_measured_hbm": halo_bytes / (hl * 1e-3) / 1e9 / peaks["hbm_gbs"]},
             "status": ctx.sync_status()}
 
 
