@@ -63,8 +63,9 @@ def test_batch_equals_cases_run_alone(prec):
             if mode == 1:
                 assert same, (k, mode)           # same kernel: bitwise
                 assert torch.equal(n1, nb[:, k])
-            else:
-                assert torch.allclose(ctx.to_compact(U), ctx.to_compact(Ub[a:e].clone()), rtol=1e-6, atol=1e-7)
+            else:   # a separately compiled kernel: equal to rounding
+                a_, b_ = ctx.to_compact(U), ctx.to_compact(Ub[a:e].clone())
+                assert (a_ - b_).abs().max() <= 2e-6 * b_.abs().max(), (k, (a_ - b_).abs().max())
 
 
 def test_batch_fp64_matches_oracle_per_case():
@@ -84,18 +85,22 @@ def test_batch_fp64_matches_oracle_per_case():
 
 
 def test_tile_shape_and_driver_do_not_change_the_state():
+    # each face is computed once from the same inputs whatever the tile shape:
+    # bitwise equal within a driver; the two drivers are separately compiled
+    # kernels and agree to rounding
     c = C.ns_ogrid8(128, 24, n_harm=2)
-    ref = None
+    ref = {}
     for mode, TI, TJ in [(0, 32, 8), (0, 32, 4), (0, 16, 8), (1, 32, 8), (1, 32, 4), (1, 16, 8)]:
         ctx = hb.HBContext(c, "fp32")
         ctx.set_tuning(mode, TI, TJ)
         U = ctx.new_state()
         ctx.init_state(U, torch.as_tensor(C.noise(c), device="cuda"), 0.01)
         ctx.rk_smooth(U, 3)
-        if ref is None:
-            ref = U.clone()
+        if mode not in ref:
+            ref[mode] = U.clone()
         else:
-            assert torch.equal(U, ref), (mode, TI, TJ)
+            assert torch.equal(U, ref[mode]), (mode, TI, TJ)
+    assert (ref[0] - ref[1]).abs().max() <= 2e-6 * ref[0].abs().max()
 
 
 def test_barrier_timeout_is_reported_and_context_recovers():
