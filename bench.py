@@ -172,10 +172,15 @@ def algorithmic_bytes_per_unit(nv, s, moving, viscous, ns):
     return state + geo * s / ns
 
 
+def _tuning_desc(mode, TI, TJ):
+    return {"driver": "persistent" if mode & 1 else "per-phase launches", "tile": [TI, TJ],
+            "ghost_fill": "halo passes" if mode & 2 else "fused into the stage"}
+
+
 def roofline(peaks, src, bpu_stage, cells_snaps, mode, launch_ms, kernel, traffic):
     """Dominant kernel: the tile kernel (one RK stage per launch) or the
     persistent driver (one RK iteration = 4 stages per launch)."""
-    stages = 4 if mode == 1 else 1
+    stages = 4 if mode & 1 else 1
     units = cells_snaps * stages
     achieved = bpu_stage * units / (launch_ms * 1e-3) / 1e9 if launch_ms > 0 else 0.0
     return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -317,9 +322,9 @@ def run_ours(args):
     bpu = algorithmic_bytes_per_unit(cs.nv, 4, True, True, cs.n_snap)
     mode, TI, TJ = r32["tuning"]
     launch_ms = r32["tile_ms"] / max(1, r32["tile_n"])
-    kname = (f"persist_kernel<float,VISC,{TI},{TJ}>" if mode == 1 else f"tile2d_kernel<float,7,VISC,RK,{TI},{TJ}>")
+    kname = (f"persist_kernel<float,VISC,{TI},{TJ}>" if mode & 1 else f"tile2d_kernel<float,7,VISC,RK,{TI},{TJ}>")
     roof = roofline(peaks, src, bpu, cs.n_cells * cs.n_snap, mode, launch_ms, kname,
-                    _traffic_record(f"{'persist' if mode == 1 else 'tile2d'}_f32_{TI}x{TJ}_ns_ogrid8"))
+                    _traffic_record(f"{'persist' if mode & 1 else 'tile2d'}_f32_{TI}x{TJ}_ns_ogrid8"))
     if rank != 0:
         return 0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -339,7 +344,7 @@ def run_ours(args):
                            "steps": args.fp64_steps,
                            "tile_launch_ms": r64["tile_ms"] / max(1, r64["tile_n"])},
             "fp32_over_fp64": value / ws / v64,
-            "tuning": {"driver": "persistent" if mode == 1 else "per-phase launches", "tile": [TI, TJ]},
+            "tuning": _tuning_desc(mode, TI, TJ),
             "batched_fp32": batch,
             "adjoint": adj,
             "box3d_fp32": box,
@@ -378,7 +383,7 @@ def run_batch(args, dev):
     return {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_iteration": ms, "iterations": K,
             "cases": len(cases), "cells": int(sum(c.n_cells for c in cases)),
             "cell_snapshots": int(sum(c.n_cells * c.n_snap for c in cases)),
-            "driver": "persistent" if mode == 1 else "per-phase launches", "tile": [TI, TJ],
+            **_tuning_desc(mode, TI, TJ),
             "status": ctx.sync_status()}
 
 
@@ -523,7 +528,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--profile", choices=["fp32", "fp64"], default=None)
     ap.add_argument("--profile-batch", action="store_true")
-    ap.add_argument("--tuning", default=None, help="mode,TI,TJ for --profile (0 per-phase, 1 persistent)")
+    ap.add_argument("--tuning", default=None,
+                    help="mode,TI,TJ (0 per-phase, 1 persistent; +2 separate halo passes instead of the fused ghost fill)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

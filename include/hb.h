@@ -205,7 +205,11 @@ hb_status hb_adjoint_residual(hb_ctx* ctx, const void* U, const void* psi, doubl
  * cache file ($HB_TUNE_CACHE, default ~/.cache/hbgpu_autotune.txt) keyed by
  * the case signature; hb_create reads that cache.  U is not modified.
  * Synchronises `stream`.  hb_set_tuning forces a choice (mode 0: per-phase
- * launches, 1: persistent); hb_get_tuning reads it. */
+ * launches, 1: persistent; + 2: separate halo passes before every stage
+ * instead of the fused ghost fill, in which each 2D tile writes the ghost
+ * cells whose value derives from its own cells right after its RK update);
+ * hb_get_tuning reads it.  The two ghost-fill forms give the same state up to
+ * rounding of the boundary maps' primitive/conservative conversions. */
 hb_status hb_autotune(hb_ctx* ctx, const void* U, int iters, void* stream);
 hb_status hb_set_tuning(hb_ctx* ctx, int mode, int TI, int TJ);
 hb_status hb_get_tuning(const hb_ctx* ctx, int* mode, int* TI, int* TJ);

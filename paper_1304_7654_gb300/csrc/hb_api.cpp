@@ -75,6 +75,17 @@ struct hb_ctx {
   int ncopy[3] = {0, 0, 0}, nbc[3] = {0, 0, 0};
   BcRec* d_walls = nullptr;
   int nwall = 0;
+  // fused ghost fill (2D): every ghost cell as a chain of boundary maps of one
+  // interior root cell, grouped by the tile that owns the root
+  bool jobs_ok = false;          // ghost jobs resolved (2D contexts)
+  bool halo_phases = false;      // tuning: run the halo passes between stages instead
+  bool fused() const { return jobs_ok && !halo_phases; }
+  struct GhostJobHost { int root_blk, root_i, root_j; hbk::GhostJob job; };
+  std::vector<GhostJobHost> gjobs;
+  hbk::GhostJob* d_jobs = nullptr;
+  int2* d_job_range = nullptr;   // [job_range_cap]
+  int job_range_cap = 0;
+  BcRec* d_job_bcs = nullptr;
   int n_bodies = 0;
   void* d_A = nullptr;          // RK ping-pong and residual scratch
   void* d_B = nullptr;
@@ -404,6 +415,61 @@ hb_status build_tables(hb_ctx* ctx, const CaseHost& ch, Tables& T) {
   return HB_OK;
 }
 
+// Resolve every ghost cell into (root interior cell, chain of boundary maps)
+// by replaying the pass-ordered fill symbolically: a cut copy passes its
+// source's chain on unchanged, a boundary record appends itself to the chain
+// of its mirror (walls) or first interior (farfield) cell.  bc_index[p] is the
+// position of Tables::bc[p][0] in the concatenated table the ops refer to.
+hb_status resolve_ghost_jobs(hb_ctx* ctx, const Tables& T, const int* bc_index) {
+  struct Res { int blk, cell, nops, op[3]; };
+  const int nb = (int)ctx->blocks.size();
+  std::vector<std::vector<Res>> res(nb);
+  for (int b = 0; b < nb; ++b) {
+    const BlockDev& B = ctx->blocks[b];
+    res[b].assign((size_t)B.plane, Res{-1, -1, 0, {-1, -1, -1}});
+    for (int j = 0; j < B.n[1]; ++j)
+      for (int i = 0; i < B.n[0]; ++i) {
+        const int c = (int)pcell(B, i, j, 0);
+        res[b][c] = Res{b, c, 0, {-1, -1, -1}};
+      }
+  }
+  for (int p = 0; p < ctx->dim; ++p) {
+    for (const CopyRec& r : T.copy[p]) {
+      const Res& src = res[r.src_blk][r.src_cell];
+      if (src.blk < 0) return fail(ctx, HB_ERR_INVALID_ARG, "ghost chain: copy from an unfilled cell");
+      res[r.dst_blk][r.dst_cell] = src;
+    }
+    for (size_t q = 0; q < T.bc[p].size(); ++q) {
+      const BcRec& r = T.bc[p][q];
+      for (int l = 0; l < 2; ++l) {
+        Res x = res[r.blk][r.type == HB_BC_FARFIELD ? r.mcell[0] : r.mcell[l]];
+        if (x.blk < 0 || x.nops >= 3) return fail(ctx, HB_ERR_INVALID_ARG, "ghost chain: unresolved boundary source");
+        x.op[x.nops++] = bc_index[p] + (int)q;
+        res[r.blk][r.gcell[l]] = x;
+      }
+    }
+  }
+  ctx->gjobs.clear();
+  for (int b = 0; b < nb; ++b) {
+    const BlockDev& B = ctx->blocks[b];
+    for (int j = -2; j < B.n[1] + 2; ++j)
+      for (int i = -2; i < B.n[0] + 2; ++i) {
+        if (i >= 0 && i < B.n[0] && j >= 0 && j < B.n[1]) continue;
+        const int c = (int)pcell(B, i, j, 0);
+        const Res& x = res[b][c];
+        if (x.blk < 0) return fail(ctx, HB_ERR_INVALID_ARG, "ghost chain: ghost cell without a root");
+        const BlockDev& R = ctx->blocks[x.blk];
+        hb_ctx::GhostJobHost g;
+        g.root_blk = x.blk;
+        g.root_i = x.cell % R.P[0] - 2;
+        g.root_j = x.cell / R.P[0] - 2;
+        g.job = hbk::GhostJob{b, c, x.cell, x.nops, {x.op[0], x.op[1], x.op[2]}, 0};
+        ctx->gjobs.push_back(g);
+      }
+  }
+  return HB_OK;
+}
+
 template <typename T>
 void fill_case_dev(const CaseHost& ch, CaseDev<T>& C) {
   const hb_case_desc& d = ch.d;
@@ -493,6 +559,9 @@ void free_ctx(hb_ctx* c) {
   cudaFree(c->d_geo);
   for (int p = 0; p < 3; ++p) { cudaFree(c->d_copy[p]); cudaFree(c->d_bc[p]); }
   cudaFree(c->d_walls);
+  cudaFree(c->d_jobs);
+  cudaFree(c->d_job_range);
+  cudaFree(c->d_job_bcs);
   cudaFree(c->d_A);
   cudaFree(c->d_B);
   cudaFree(c->d_partials);
@@ -568,6 +637,36 @@ hb_status rebuild_tiles(hb_ctx* c, int TI, int TJ) {
   }
   HB_CUDA(c, cudaMemcpy(c->d_tiles, tiles.data(), sizeof(int4) * n, cudaMemcpyHostToDevice));
   HB_CUDA(c, cudaMemcpy(c->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  if (c->jobs_ok) {
+    // ghost jobs grouped by the tile owning the root, in destination order within a tile
+    std::vector<int> first_tile(c->blocks.size(), 0), tiles_i(c->blocks.size(), 1);
+    for (int q = n - 1; q >= 0; --q) first_tile[tiles[q].x] = q;
+    for (size_t b = 0; b < c->blocks.size(); ++b) tiles_i[b] = (c->blocks[b].n[0] + TI - 1) / TI;
+    std::vector<std::pair<int, int>> key(c->gjobs.size());
+    for (size_t q = 0; q < c->gjobs.size(); ++q) {
+      const auto& g = c->gjobs[q];
+      key[q] = {first_tile[g.root_blk] + (g.root_j / TJ) * tiles_i[g.root_blk] + g.root_i / TI, (int)q};
+    }
+    std::stable_sort(key.begin(), key.end());
+    std::vector<hbk::GhostJob> jobs(key.size());
+    std::vector<int2> range(std::max(1, n), make_int2(0, 0));
+    for (size_t q = 0; q < key.size(); ++q) {
+      jobs[q] = c->gjobs[key[q].second].job;
+      int2& r = range[key[q].first];
+      if (r.y == 0) r.x = (int)q;
+      r.y++;
+    }
+    if (!c->d_jobs && !jobs.empty()) HB_CUDA(c, cudaMalloc(&c->d_jobs, sizeof(hbk::GhostJob) * jobs.size()));
+    if (n > c->job_range_cap) {
+      cudaFree(c->d_job_range);
+      c->d_job_range = nullptr;
+      HB_CUDA(c, cudaMalloc(&c->d_job_range, sizeof(int2) * std::max(1, n)));
+      c->job_range_cap = n;
+    }
+    if (!jobs.empty())
+      HB_CUDA(c, cudaMemcpy(c->d_jobs, jobs.data(), sizeof(hbk::GhostJob) * jobs.size(), cudaMemcpyHostToDevice));
+    HB_CUDA(c, cudaMemcpy(c->d_job_range, range.data(), sizeof(int2) * std::max(1, n), cudaMemcpyHostToDevice));
+  }
   if (!c->d_case_tile0) {
     HB_CUDA(c, cudaMalloc(&c->d_case_tile0, sizeof(int) * c->cases.size()));
     HB_CUDA(c, cudaMalloc(&c->d_case_ntiles, sizeof(int) * c->cases.size()));
@@ -761,6 +860,21 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
       CK(cudaMemcpy(ctx->d_bc[p], Tb.bc[p].data(), sizeof(BcRec) * ctx->nbc[p], cudaMemcpyHostToDevice));
     }
   }
+  if (ctx->dim == 2) {
+    int bc_index[3] = {0, 0, 0};
+    std::vector<BcRec> all;
+    for (int p = 0; p < 3; ++p) {
+      bc_index[p] = (int)all.size();
+      all.insert(all.end(), Tb.bc[p].begin(), Tb.bc[p].end());
+    }
+    hb_status s = resolve_ghost_jobs(ctx, Tb, bc_index);
+    if (s != HB_OK) return bad(s, ctx->err);
+    if (!all.empty()) {
+      CK(cudaMalloc(&ctx->d_job_bcs, sizeof(BcRec) * all.size()));
+      CK(cudaMemcpy(ctx->d_job_bcs, all.data(), sizeof(BcRec) * all.size(), cudaMemcpyHostToDevice));
+    }
+    ctx->jobs_ok = true;
+  }
   ctx->nwall = (int)Tb.walls.size();
   if (ctx->nwall) {
     CK(cudaMalloc(&ctx->d_walls, sizeof(BcRec) * ctx->nwall));
@@ -791,6 +905,7 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
                       std::to_string(ctx->viscous) + "_c" + std::to_string(ctx->cases.size()) + "_n" +
                       std::to_string(ctx->total_cells) + "_b" + std::to_string(ctx->blocks.size()) + "_s";
     for (auto& ch : ctx->cases) key += std::to_string(ch.ns);
+    key += "_g1";   // drivers with the fused ghost fill
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -911,10 +1026,13 @@ hb_status stage_all(hb_ctx* c, hbk::StageParams<T> p, int mode, cudaStream_t s) 
     p.ntiles = ch.ntiles;
     double* part = p.partials;
     if (part) p.partials = part + (size_t)8 * ch.tile0;
+    const int2* jr = p.job_range;
+    if (jr) p.job_range = jr + ch.tile0;
     TimedScope ts(c, 0, s);
     if (c->dim == 3) HB_CUDA(c, hbk::launch_stage3d<T>(p, ch.ns, c->viscous, mode, s));
     else HB_CUDA(c, hbk::launch_stage<T>(p, ch.ns, c->viscous, mode, s));
     p.partials = part;
+    p.job_range = jr;
   }
   return HB_OK;
 }
@@ -940,10 +1058,16 @@ hb_status rk_iteration(hb_ctx* c, T* U, double* norm_out, cudaStream_t s) {
   T* Bf = (T*)c->d_B;
   T* in[4] = {U, A, Bf, A};
   T* out[4] = {A, Bf, A, U};
+  const bool fused = c->fused();
   for (int st = 0; st < 4; ++st) {
-    hb_status r = halos<T>(c, in[st], s);
+    hb_status r = fused ? HB_OK : halos<T>(c, in[st], s);   // fused: the previous stage filled them
     if (r != HB_OK) return r;
     auto p = stage_params<T>(c);
+    if (fused) {
+      p.job_range = c->d_job_range;
+      p.jobs = c->d_jobs;
+      p.job_bcs = c->d_job_bcs;
+    }
     p.Uprev = in[st];
     p.U0 = U;
     p.Unext = out[st];
@@ -985,7 +1109,13 @@ hb_status persist_chunk(hb_ctx* c, T* U, int K, cudaStream_t s) {
     p.st[st].Unext = out[st];
     p.st[st].alpha = (T)alpha[st];
     p.st[st].partials = (st == 0) ? c->d_partials : nullptr;
+    if (c->fused()) {
+      p.st[st].job_range = c->d_job_range;
+      p.st[st].jobs = c->d_jobs;
+      p.st[st].job_bcs = c->d_job_bcs;
+    }
   }
+  p.fused = c->fused() ? 1 : 0;
   for (int pass = 0; pass < c->dim; ++pass) {
     hbk::HaloParams<T>& h = p.halo[pass];
     h.cases = (const CaseDev<T>*)c->d_cases;
@@ -1030,6 +1160,10 @@ hb_status copy_norms(hb_ctx* c, double* norms, int done, int K, cudaStream_t s) 
 
 template <typename T>
 hb_status rk_chunk_direct(hb_ctx* c, T* U, int K, cudaStream_t s) {
+  if (c->fused()) {   // the stages keep the halos filled from here on
+    hb_status r = halos<T>(c, U, s);
+    if (r != HB_OK) return r;
+  }
   if (c->mode == 1 && hbk::persist_available<T>(c->TI, c->TJ)) return persist_chunk<T>(c, U, K, s);
   const size_t nc = c->cases.size();
   for (int k = 0; k < K; ++k) {
@@ -1101,6 +1235,7 @@ hb_status autotune_impl(hb_ctx* c, const T* U, int iters, cudaStream_t s) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
+  c->halo_phases = false;
   int bm = c->mode, bi = c->TI, bj = c->TJ;
   hb_status st = HB_OK;
   const int shapes[3][2] = {{32, 8}, {32, 4}, {16, 8}};
@@ -1309,7 +1444,9 @@ hb_status hb_autotune(hb_ctx* ctx, const void* U, int iters, void* stream) {
 }
 
 hb_status hb_set_tuning(hb_ctx* ctx, int mode, int TI, int TJ) {
-  if (!ctx || mode < 0 || mode > 1) return fail(ctx, HB_ERR_INVALID_ARG, "bad tuning");
+  if (!ctx || mode < 0 || mode > 3) return fail(ctx, HB_ERR_INVALID_ARG, "bad tuning");
+  const bool phases = (mode & 2) != 0;
+  mode &= 1;
   if (ctx->dim == 3) return fail(ctx, HB_ERR_UNSUPPORTED, "3D contexts use fixed 8x8x4 tiles, one launch per phase");
   const bool ok = (TI == 32 && TJ == 8) || (TI == 32 && TJ == 4) || (TI == 16 && TJ == 8);
   if (!ok) return fail(ctx, HB_ERR_UNSUPPORTED, "tile shape not built");
@@ -1319,12 +1456,13 @@ hb_status hb_set_tuning(hb_ctx* ctx, int mode, int TI, int TJ) {
   hb_status st = rebuild_tiles(ctx, TI, TJ);
   if (st != HB_OK) return st;
   ctx->mode = mode;
+  ctx->halo_phases = phases;
   return HB_OK;
 }
 
 hb_status hb_get_tuning(const hb_ctx* ctx, int* mode, int* TI, int* TJ) {
   if (!ctx) return HB_ERR_INVALID_ARG;
-  if (mode) *mode = ctx->mode;
+  if (mode) *mode = ctx->mode | (ctx->halo_phases ? 2 : 0);
   if (TI) *TI = ctx->TI;
   if (TJ) *TJ = ctx->TJ;
   return HB_OK;

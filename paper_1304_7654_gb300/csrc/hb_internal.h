@@ -62,6 +62,13 @@ struct BcRec {
   int body;
 };
 
+// A ghost cell whose value is a chain of at most three physical-boundary maps
+// (op: index into the stage's BcRec table, applied in order) of one interior
+// cell (root_cell, in the block of the tile that owns it).  Cut copies are the
+// identity and leave no op.  After an RK stage the tile that wrote the root
+// writes the ghost, so the next stage finds every halo filled.
+struct GhostJob { int dst_blk, dst_cell, root_cell, nops, op[3], pad; };
+
 template <typename T>
 struct Geo {
   const T* q[G_NQ];
@@ -81,6 +88,9 @@ struct StageParams {
   double* partials;        // [ntiles][8] FP64 norm partials, or null
   T alpha;                 // RK stage coefficient
   int TI, TJ, ti_shift;    // tile shape; TI = 1 << ti_shift
+  const int2* job_range;   // RK mode: [ntiles] (first, count) into jobs, or null (no fused ghost fill)
+  const GhostJob* jobs;
+  const BcRec* job_bcs;
 };
 
 template <typename T>
@@ -134,6 +144,7 @@ struct PersistParams {
   double* norms;            // [K][ncases][8] or null
   long long timeout_ns;     // barrier wait limit
   int skip_cta;             // test hook: this CTA does not arrive at the first barrier (-1: none)
+  int fused;                // 1: the stages fill the halos of their output (no halo phases)
 };
 
 // launchers (defined per precision in hb_kernels_f32.cu / hb_kernels_f64.cu)

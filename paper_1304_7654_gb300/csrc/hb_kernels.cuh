@@ -198,6 +198,153 @@ __device__ __forceinline__ void block_sum8(double* v, int nv, double* scratch) {
   }
 }
 
+// ------------------------------------------------------------- halos/BCs --
+template <typename T>
+__device__ __forceinline__ void freestream_at(const CaseDev<T>* C, int n, T x, T* W) {
+  W[0] = C->winf[n][0];
+  W[1] = C->winf[n][1];
+  W[2] = C->winf[n][2];
+  W[3] = C->winf[n][3];
+  W[4] = C->winf[n][4];
+  if (C->ubc == 2) W[2] += C->ubc_amp * C->mach * sin(C->tn[n] - C->omega * x / C->mach);
+}
+
+// conservative <-> primitive (rho, u, v, w, p); w = 0 in 2D
+template <typename T, int DIM>
+__device__ __forceinline__ void prim_of(const T* Q, T gm1, T* W) {
+  constexpr int NV = DIM + 2;
+  const T rho = Q[0];
+  W[0] = rho;
+  W[1] = Q[1] / rho;
+  W[2] = Q[2] / rho;
+  W[3] = (DIM == 3) ? Q[3] / rho : T(0);
+  W[4] = gm1 * (Q[NV - 1] - T(0.5) * rho * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]));
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ void cons_of(const T* W, T gm1, T* Q) {
+  constexpr int NV = DIM + 2;
+  Q[0] = W[0];
+  Q[1] = W[0] * W[1];
+  Q[2] = W[0] * W[2];
+  if (DIM == 3) Q[3] = W[0] * W[3];
+  Q[NV - 1] = W[4] / gm1 + T(0.5) * W[0] * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
+}
+
+// primitives of a padded cell of a block at one snapshot (Ub: snapshot base)
+template <typename T, int DIM>
+__device__ __forceinline__ void load_prim(const T* Ub, int64_t plane, int64_t cell, T gm1, T* W) {
+  constexpr int NV = DIM + 2;
+  T Q[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Q[v] = Ub[v * plane + cell];
+  prim_of<T, DIM>(Q, gm1, W);
+}
+
+template <typename T, int DIM>
+__device__ __forceinline__ void store_cons(T* Ub, int64_t plane, int64_t cell, T gm1, const T* W) {
+  constexpr int NV = DIM + 2;
+  T Q[NV];
+  cons_of<T, DIM>(W, gm1, Q);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Ub[v * plane + cell] = Q[v];
+}
+
+// Physical-boundary ghost state at snapshot n from Wi: type 1 characteristic
+// farfield (Wi = first interior cell; Riemann invariants normal to the face,
+// entropy and tangential velocity from inside on outflow, from the freestream
+// on inflow), type 2 slip wall (Wi = mirror cell; relative normal velocity
+// reflected), type 3 no-slip adiabatic wall (u_g = 2 v_wall - u).  The
+// boundary face is the low face along p of padded cell fcell; sgn = +1 on a
+// high face, -1 on a low face.
+template <typename T, int DIM>
+__device__ __forceinline__ void bc_map(const CaseDev<T>* C, const Geo<T>& g, const BlockDev& B, int type, int p,
+                                       int sgn, int fcell, int n, const T* Wi, T* Wg) {
+  const Fr<T> f = frame_at(C, n);
+  const T gam = C->gamma, gm1 = gam - T(1);
+  const int64_t fc = B.goff + fcell;
+  T S[3] = {g.q[G_S + 3 * p][fc], g.q[G_S + 3 * p + 1][fc], T(0)};
+  T X[3] = {g.q[G_XF + 3 * p][fc], g.q[G_XF + 3 * p + 1][fc], T(0)};
+  if (DIM == 3) {
+    S[2] = g.q[G_S + 3 * p + 2][fc];
+    X[2] = g.q[G_XF + 3 * p + 2][fc];
+  }
+  T sr[3], xr[3];
+  rotv(f, S[0], S[1], sr[0], sr[1]);
+  sr[2] = S[2];
+  rotp(f, X[0], X[1], xr[0], xr[1]);
+  xr[2] = X[2];
+  const T vg[3] = {-f.thd * (xr[1] - f.py), f.thd * (xr[0] - f.px), T(0)};
+  const T A = sqrt(sr[0] * sr[0] + sr[1] * sr[1] + sr[2] * sr[2]);
+  const T sg = T(sgn);
+  const T nr[3] = {sg * sr[0] / A, sg * sr[1] / A, sg * sr[2] / A};
+  if (type == 1) {
+    T Wf[5];
+    freestream_at(C, n, xr[0], Wf);
+    const T qi = (Wi[1] - vg[0]) * nr[0] + (Wi[2] - vg[1]) * nr[1] + (Wi[3] - vg[2]) * nr[2];
+    const T qf = (Wf[1] - vg[0]) * nr[0] + (Wf[2] - vg[1]) * nr[1] + (Wf[3] - vg[2]) * nr[2];
+    const T ci = sqrt(gam * Wi[4] / Wi[0]), cf = sqrt(gam * Wf[4] / Wf[0]);
+    const T Rp = qi + T(2) * ci / gm1, Rm = qf - T(2) * cf / gm1;
+    const T qb = T(0.5) * (Rp + Rm);
+    const T cb = T(0.25) * gm1 * (Rp - Rm);
+    const bool outflow = qb > T(0);
+    T Wr[5];
+#pragma unroll
+    for (int a = 0; a < 5; ++a) Wr[a] = outflow ? Wi[a] : Wf[a];
+    const T qr = outflow ? qi : qf;
+    const T ent = Wr[4] / pow(Wr[0], gam);
+    Wg[0] = pow(cb * cb / (gam * ent), T(1) / gm1);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Wg[1 + a] = vg[a] + ((Wr[1 + a] - vg[a]) - qr * nr[a]) + qb * nr[a];
+    Wg[4] = Wg[0] * cb * cb / gam;
+  } else {
+    Wg[0] = Wi[0];
+    Wg[4] = Wi[4];
+    if (type == 2) {
+      const T qn = (Wi[1] - vg[0]) * nr[0] + (Wi[2] - vg[1]) * nr[1] + (Wi[3] - vg[2]) * nr[2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Wg[1 + a] = Wi[1 + a] - T(2) * qn * nr[a];
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Wg[1 + a] = T(2) * vg[a] - Wi[1 + a];
+    }
+  }
+  if (DIM == 2) Wg[3] = T(0);
+}
+
+// Fused ghost fill after an RK stage: the ghost cells whose root is an own
+// cell of tile t, at every snapshot, from the stage output just written.
+template <typename T, int NS>
+__device__ __forceinline__ void fill_tile_ghosts(const StageParams<T>& P, int t, const BlockDev& B,
+                                                 const CaseDev<T>* C) {
+  constexpr int NV = 4;
+  const int2 jr = P.job_range[t];
+  if (jr.y <= 0) return;
+  __syncthreads();   // own-cell outputs of every thread of the CTA are visible
+  const T gm1 = C->gamma - T(1);
+  const int nitem = jr.y * NS;
+  for (int w = threadIdx.x; w < nitem; w += blockDim.x) {
+    const int n = w / jr.y;
+    const GhostJob* J = P.jobs + jr.x + (w - n * jr.y);
+    const T* src = P.Unext + B.off + (int64_t)n * NV * B.plane + J->root_cell;
+    T Q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Q[v] = src[v * B.plane];
+    const int nops = J->nops;
+    for (int k = 0; k < nops; ++k) {
+      const BcRec& r = P.job_bcs[J->op[k]];
+      T Wi[5], Wg[5];
+      prim_of<T, 2>(Q, gm1, Wi);
+      bc_map<T, 2>(C, P.g, P.blocks[r.blk], r.type, r.p, r.sgn, r.fcell, n, Wi, Wg);
+      cons_of<T, 2>(Wg, gm1, Q);
+    }
+    const BlockDev& D = P.blocks[J->dst_blk];
+    T* dst = P.Unext + D.off + (int64_t)n * NV * D.plane + J->dst_cell;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dst[v * D.plane] = Q[v];
+  }
+}
+
 // MODE 0: R := residual.  MODE 1: RK stage update (+ norm partials if set).
 // The tile shape TI x TJ (TI a power of two) is a compile-time constant so that
 // every flat-index decomposition is a multiply-shift.
@@ -470,6 +617,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
     if (threadIdx.x == 0)
       for (int q = 0; q < NV; ++q) P.partials[(int64_t)t * 8 + q] = nacc[q];
   }
+  if (MODE == 1 && P.job_range) fill_tile_ghosts<T, NS>(P, t, B, C);
 }
 
 template <typename T, int NS, bool VISC, int MODE, int TI, int TJ>
@@ -484,17 +632,7 @@ constexpr int kTileShapes = 3;
 __host__ __device__ constexpr int tile_ti(int id) { return id == 0 ? 32 : (id == 1 ? 32 : 16); }
 __host__ __device__ constexpr int tile_tj(int id) { return id == 0 ? 8 : (id == 1 ? 4 : 8); }
 
-// ------------------------------------------------------------- halos/BCs --
-template <typename T>
-__device__ __forceinline__ void freestream_at(const CaseDev<T>* C, int n, T x, T* W) {
-  W[0] = C->winf[n][0];
-  W[1] = C->winf[n][1];
-  W[2] = C->winf[n][2];
-  W[3] = C->winf[n][3];
-  W[4] = C->winf[n][4];
-  if (C->ubc == 2) W[2] += C->ubc_amp * C->mach * sin(C->tn[n] - C->omega * x / C->mach);
-}
-
+// ------------------------------------------------------------- halo kernel --
 // one work item per (record, snapshot), snapshot-major so that neighbouring
 // threads touch neighbouring cells
 template <typename T, int DIM>
@@ -520,78 +658,20 @@ __device__ __forceinline__ void halo_item(const HaloParams<T>& p, int64_t gid) {
   const BlockDev& B = p.blocks[r.blk];
   const CaseDev<T>* C = p.cases + B.cs;
   if (n >= C->ns) return;
-  const Fr<T> f = frame_at(C, n);
-  const T gam = C->gamma, gm1 = gam - T(1);
-  const int64_t fc = B.goff + r.fcell;
-  T S[3] = {p.g.q[G_S + 3 * r.p][fc], p.g.q[G_S + 3 * r.p + 1][fc], T(0)};
-  T X[3] = {p.g.q[G_XF + 3 * r.p][fc], p.g.q[G_XF + 3 * r.p + 1][fc], T(0)};
-  if (DIM == 3) {
-    S[2] = p.g.q[G_S + 3 * r.p + 2][fc];
-    X[2] = p.g.q[G_XF + 3 * r.p + 2][fc];
-  }
-  T sr[3], xr[3];
-  rotv(f, S[0], S[1], sr[0], sr[1]);
-  sr[2] = S[2];
-  rotp(f, X[0], X[1], xr[0], xr[1]);
-  xr[2] = X[2];
-  const T vg[3] = {-f.thd * (xr[1] - f.py), f.thd * (xr[0] - f.px), T(0)};
-  const T A = sqrt(sr[0] * sr[0] + sr[1] * sr[1] + sr[2] * sr[2]);
-  const T sg = T(r.sgn);
-  const T nr[3] = {sg * sr[0] / A, sg * sr[1] / A, sg * sr[2] / A};
+  const T gm1 = C->gamma - T(1);
   T* Ub = p.U + B.off + (int64_t)n * NV * B.plane;
-  auto load = [&](int cell, T* W) {
-    const T rho = Ub[cell];
-    W[0] = rho;
-    W[1] = Ub[B.plane + cell] / rho;
-    W[2] = Ub[2 * B.plane + cell] / rho;
-    W[3] = (DIM == 3) ? Ub[3 * B.plane + cell] / rho : T(0);
-    W[4] = gm1 * (Ub[(NV - 1) * B.plane + cell] - T(0.5) * rho * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]));
-  };
-  auto store = [&](int cell, const T* W) {
-    Ub[cell] = W[0];
-    Ub[B.plane + cell] = W[0] * W[1];
-    Ub[2 * B.plane + cell] = W[0] * W[2];
-    if (DIM == 3) Ub[3 * B.plane + cell] = W[0] * W[3];
-    Ub[(NV - 1) * B.plane + cell] = W[4] / gm1 + T(0.5) * W[0] * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]);
-  };
-  if (r.type == 1) {   // characteristic farfield (Riemann invariants normal to the face)
-    T Wi[5], Wf[5];
-    load(r.mcell[0], Wi);
-    freestream_at(C, n, xr[0], Wf);
-    const T qi = (Wi[1] - vg[0]) * nr[0] + (Wi[2] - vg[1]) * nr[1] + (Wi[3] - vg[2]) * nr[2];
-    const T qf = (Wf[1] - vg[0]) * nr[0] + (Wf[2] - vg[1]) * nr[1] + (Wf[3] - vg[2]) * nr[2];
-    const T ci = sqrt(gam * Wi[4] / Wi[0]), cf = sqrt(gam * Wf[4] / Wf[0]);
-    const T Rp = qi + T(2) * ci / gm1, Rm = qf - T(2) * cf / gm1;
-    const T qb = T(0.5) * (Rp + Rm);
-    const T cb = T(0.25) * gm1 * (Rp - Rm);
-    const T* Wr = (qb > T(0)) ? Wi : Wf;
-    const T qr = (qb > T(0)) ? qi : qf;
-    const T ent = Wr[4] / pow(Wr[0], gam);
-    T Wg[5];
-    Wg[0] = pow(cb * cb / (gam * ent), T(1) / gm1);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) Wg[1 + a] = vg[a] + ((Wr[1 + a] - vg[a]) - qr * nr[a]) + qb * nr[a];
-    if (DIM == 2) Wg[3] = T(0);
-    Wg[4] = Wg[0] * cb * cb / gam;
-    store(r.gcell[0], Wg);
-    store(r.gcell[1], Wg);
-  } else {
+  T Wi[5], Wg[5];
+  if (r.type == 1) {   // farfield: both ghost layers from the first interior cell
+    load_prim<T, DIM>(Ub, B.plane, r.mcell[0], gm1, Wi);
+    bc_map<T, DIM>(C, p.g, B, r.type, r.p, r.sgn, r.fcell, n, Wi, Wg);
+    store_cons<T, DIM>(Ub, B.plane, r.gcell[0], gm1, Wg);
+    store_cons<T, DIM>(Ub, B.plane, r.gcell[1], gm1, Wg);
+  } else {             // walls: each ghost layer mirrors its own interior layer
 #pragma unroll
     for (int l = 0; l < 2; ++l) {
-      T Wm[5], Wg[5];
-      load(r.mcell[l], Wm);
-      Wg[0] = Wm[0];
-      Wg[4] = Wm[4];
-      if (r.type == 2) {   // slip wall: reflect the relative normal velocity
-        const T qn = (Wm[1] - vg[0]) * nr[0] + (Wm[2] - vg[1]) * nr[1] + (Wm[3] - vg[2]) * nr[2];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) Wg[1 + a] = Wm[1 + a] - T(2) * qn * nr[a];
-      } else {             // no-slip adiabatic wall: u_g = 2 v_wall - u
-#pragma unroll
-        for (int a = 0; a < 3; ++a) Wg[1 + a] = T(2) * vg[a] - Wm[1 + a];
-      }
-      if (DIM == 2) Wg[3] = T(0);
-      store(r.gcell[l], Wg);
+      load_prim<T, DIM>(Ub, B.plane, r.mcell[l], gm1, Wi);
+      bc_map<T, DIM>(C, p.g, B, r.type, r.p, r.sgn, r.fcell, n, Wi, Wg);
+      store_cons<T, DIM>(Ub, B.plane, r.gcell[l], gm1, Wg);
     }
   }
 }

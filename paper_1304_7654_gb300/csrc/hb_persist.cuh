@@ -1,6 +1,8 @@
 // Persistent batched RK driver: one cooperative launch runs K iterations of
 // every case of a batch (different grids, N_H, Mach and motion): per stage,
-// the halo passes and then all tiles, each phase closed by a grid barrier.
+// all tiles, closed by a grid barrier.  The tiles fill the halos of their
+// output themselves (fused ghost fill), so a stage needs one barrier; without
+// the ghost tables each stage first runs the halo passes, one barrier each.
 // The barrier spins with a wall-clock limit (globaltimer); on expiry it sets
 // HB_ERR_TIMEOUT and an abort flag, every CTA leaves at its next barrier, and
 // the kernel returns -- it never traps.  Tiles are claimed through an atomic
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(TI * TJ, (sizeof(T) == 4 ? 3 : 1) * (MAXNT / (
   int nbar = 0;
   for (int it = 0; it < P.K; ++it) {
     for (int s = 0; s < 4; ++s) {
-      for (int pass = 0; pass < P.dim; ++pass) {
+      for (int pass = 0; pass < (P.fused ? 0 : P.dim); ++pass) {
         HaloParams<T> hp = P.halo[pass];
         hp.U = const_cast<T*>(P.st[s].Uprev);
         const int64_t tot = ((int64_t)hp.ncopy + hp.nbc) * hp.ns_max;
