@@ -172,6 +172,16 @@ def algorithmic_bytes_per_unit(nv, s, moving, viscous, ns):
     return state + geo * s / ns
 
 
+def _checked_status(ctx, what):
+    """A run whose state went non-finite (or whose barrier timed out) is not
+    a measurement: fail loudly instead of printing its time."""
+    from paper_1304_7654_gb300 import hb
+    st = ctx.sync_status()
+    if st != hb.HB_OK:
+        raise RuntimeError(f"{what} run ended with status {st}: not a valid measurement")
+    return st
+
+
 def _tuning_desc(mode, TI, TJ):
     return {"driver": "persistent" if mode & 1 else "per-phase launches", "tile": [TI, TJ],
             "ghost_fill": "halo passes" if mode & 2 else "fused into the stage"}
@@ -256,6 +266,8 @@ def run_ours(args):
         _, launches = ctx.kernel_stats(2)
         ctx.set_timing(False)
         st = ctx.sync_status()
+        if st != hb.HB_OK:
+            raise RuntimeError(f"{prec} run ended with status {st} (non-finite state): not a valid measurement")
         return dict(ms=ms, wall=wall, tile_ms=tile_ms, tile_n=tile_n, halo_ms=halo_ms, halo_n=halo_n,
                     launches=launches, status=st, ctx=ctx, U=U, tuning=ctx.tuning())
 
@@ -384,7 +396,7 @@ def run_batch(args, dev):
             "cases": len(cases), "cells": int(sum(c.n_cells for c in cases)),
             "cell_snapshots": int(sum(c.n_cells * c.n_snap for c in cases)),
             **_tuning_desc(mode, TI, TJ),
-            "status": ctx.sync_status()}
+            "status": _checked_status(ctx, "batched FP32")}
 
 
 def run_box3d(args, dev):
@@ -427,7 +439,7 @@ def run_box3d(args, dev):
                             "frac_of_measured_hbm": tile_bytes / (tl * 1e-3) / 1e9 / peaks["hbm_gbs"]},
             "halo_kernel": {"launch_ms": hl, "algorithmic_GBs": halo_bytes / (hl * 1e-3) / 1e9,
                             "frac_of_measured_hbm": halo_bytes / (hl * 1e-3) / 1e9 / peaks["hbm_gbs"]},
-            "status": ctx.sync_status()}
+            "status": _checked_status(ctx, "3D box")}
 
 
 def adjoint_ratio(dev):

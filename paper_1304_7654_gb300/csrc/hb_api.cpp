@@ -586,44 +586,131 @@ void free_ctx(hb_ctx* c) {
 
 constexpr int kMaxK = 64;   // iterations per persistent launch / graph
 
-// Tile work list for shape TI x TJ: tiles of every case in case order, the
-// claim order (cost = snapshots x cells, largest first) and per-case ranges.
-hb_status rebuild_tiles(hb_ctx* c, int TI, int TJ) {
+// Concurrent CTAs of the RK-stage work for a case (mode 0: its own launch)
+// or for the whole batch (mode 1: the persistent grid); 0 if unknown.
+int wave_slots(hb_ctx* c, int mode, int ns, int TI, int TJ) {
+  int slots = 0;
+  cudaError_t e;
+  if (mode == 1) {
+    if (!(c->prec == HB_FP32 ? hbk::persist_available<float>(TI, TJ) : hbk::persist_available<double>(TI, TJ)))
+      return 0;
+    if (c->prec == HB_FP32) {
+      hbk::PersistParams<float> p{};
+      p.ns_max = c->ns_max;   // K = 0: query only
+      e = hbk::launch_persist<float>(p, c->viscous, TI, TJ, nullptr, &slots);
+    } else {
+      hbk::PersistParams<double> p{};
+      p.ns_max = c->ns_max;
+      e = hbk::launch_persist<double>(p, c->viscous, TI, TJ, nullptr, &slots);
+    }
+  } else {
+    e = c->prec == HB_FP32 ? hbk::stage_slots<float>(ns, c->viscous, TI, TJ, &slots)
+                           : hbk::stage_slots<double>(ns, c->viscous, TI, TJ, &slots);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return slots;
+}
+
+// Split the tiles that would run in a final partial wave into row strips.
+// With N tiles in dispatch order and S concurrent CTAs, the last N mod S
+// tiles run alone after the full waves, each taking a full tile time; as q
+// strips of TJ/q rows (q * (N mod S) <= S) they finish in a fraction of it.
+// Strips of at least two rows: thinner ones cost as much as two-row strips.
+void split_tail(std::vector<int4>& tl, const std::vector<int>& dispatch, int S, int TJ) {
+  const int N = (int)dispatch.size();
+  if (S <= 0 || N == 0) return;
+  const int r = N % S;
+  if (r == 0) return;
+  int q = 1;
+  while (q * 2 <= TJ / 2 && (long long)r * q * 2 <= S) q *= 2;
+  if (q == 1) return;
+  std::vector<char> cut(tl.size(), 0);
+  for (int k = N - r; k < N; ++k) cut[dispatch[k]] = 1;
+  std::vector<int4> out;
+  out.reserve(tl.size() + (size_t)r * (q - 1));
+  for (size_t k = 0; k < tl.size(); ++k) {
+    const int4 t = tl[k];
+    if (!cut[k] || t.w < 2) {
+      out.push_back(t);
+      continue;
+    }
+    const int h = (t.w + q - 1) / q;
+    for (int j = 0; j < t.w; j += h) out.push_back(make_int4(t.x, t.y, t.z + j, std::min(h, t.w - j)));
+  }
+  tl.swap(out);
+}
+
+// Tile work list for shape TI x TJ: tiles of every case in case order (2D
+// tiles carry their row count in .w; the tail of a wave is split into row
+// strips for the driver `mode`), the claim order (cost = snapshots x cells,
+// largest first) and per-case ranges.
+hb_status rebuild_tiles(hb_ctx* c, int TI, int TJ, int mode) {
   std::vector<int4> tiles;
   std::vector<int> t0(c->cases.size()), nt(c->cases.size());
   std::vector<double> inv(c->cases.size());
-  std::vector<std::pair<long long, int>> cost;
+  std::vector<long long> tcost;
+  auto cells_of = [&](const int4& t) -> long long {
+    const BlockDev& B = c->blocks[t.x];
+    if (c->dim == 3)
+      return (long long)std::min(8, B.n[0] - t.y) * std::min(8, B.n[1] - t.z) * std::min(4, B.n[2] - t.w);
+    return (long long)std::min(TI, B.n[0] - t.y) * t.w;
+  };
   for (size_t k = 0; k < c->cases.size(); ++k) {
     CaseHost& ch = c->cases[k];
     ch.tile0 = (int)tiles.size();
+    std::vector<int4> ct;
     for (int b = 0; b < ch.nblocks; ++b) {
       const BlockDev& B = c->blocks[ch.block0 + b];
       if (c->dim == 3) {   // fixed 8 x 8 x 4 tiles
         for (int k = 0; k < B.n[2]; k += 4)
           for (int j = 0; j < B.n[1]; j += 8)
-            for (int i = 0; i < B.n[0]; i += 8) {
-              const long long cells = (long long)std::min(8, B.n[0] - i) * std::min(8, B.n[1] - j) *
-                                      std::min(4, B.n[2] - k);
-              cost.push_back({-(cells * ch.ns), (int)tiles.size()});
-              tiles.push_back(make_int4(ch.block0 + b, i, j, k));
-            }
+            for (int i = 0; i < B.n[0]; i += 8) ct.push_back(make_int4(ch.block0 + b, i, j, k));
         continue;
       }
       for (int j = 0; j < B.n[1]; j += TJ)
-        for (int i = 0; i < B.n[0]; i += TI) {
-          const long long cells = (long long)std::min(TI, B.n[0] - i) * std::min(TJ, B.n[1] - j);
-          cost.push_back({-(cells * ch.ns), (int)tiles.size()});
-          tiles.push_back(make_int4(ch.block0 + b, i, j, 0));
-        }
+        for (int i = 0; i < B.n[0]; i += TI) ct.push_back(make_int4(ch.block0 + b, i, j, std::min(TJ, B.n[1] - j)));
     }
+    if (c->dim == 2 && mode == 0) {   // this case's launch dispatches its tiles in list order
+      std::vector<int> disp(ct.size());
+      for (size_t q = 0; q < ct.size(); ++q) disp[q] = (int)q;
+      split_tail(ct, disp, wave_slots(c, 0, ch.ns, TI, TJ), TJ);
+    }
+    tiles.insert(tiles.end(), ct.begin(), ct.end());
+    for (const int4& t : ct) tcost.push_back(cells_of(t) * ch.ns);
     ch.ntiles = (int)tiles.size() - ch.tile0;
     t0[k] = ch.tile0;
     nt[k] = ch.ntiles;
     inv[k] = 1.0 / ((double)ch.cells * ch.ns);
   }
-  std::stable_sort(cost.begin(), cost.end());
-  std::vector<int> order(cost.size());
-  for (size_t q = 0; q < cost.size(); ++q) order[q] = cost[q].second;
+  auto claim_order = [&]() {
+    std::vector<std::pair<long long, int>> cost(tiles.size());
+    for (size_t q = 0; q < tiles.size(); ++q) cost[q] = {-tcost[q], (int)q};
+    std::stable_sort(cost.begin(), cost.end());
+    std::vector<int> order(cost.size());
+    for (size_t q = 0; q < cost.size(); ++q) order[q] = cost[q].second;
+    return order;
+  };
+  std::vector<int> order = claim_order();
+  if (c->dim == 2 && mode == 1) {   // one persistent grid claims all tiles in cost order
+    const size_t before = tiles.size();
+    split_tail(tiles, order, wave_slots(c, 1, c->ns_max, TI, TJ), TJ);
+    if (tiles.size() != before) {   // per-case ranges and costs of the new list
+      tcost.clear();
+      size_t q = 0;
+      for (size_t k = 0; k < c->cases.size(); ++k) {
+        CaseHost& ch = c->cases[k];
+        ch.tile0 = (int)q;
+        while (q < tiles.size() && c->blocks[tiles[q].x].cs == (int)k) tcost.push_back(cells_of(tiles[q++]) * ch.ns);
+        ch.ntiles = (int)q - ch.tile0;
+        t0[k] = ch.tile0;
+        nt[k] = ch.ntiles;
+      }
+      order = claim_order();
+    }
+  }
   const int n = (int)tiles.size();
   if (n > c->max_tiles) {
     cudaFree(c->d_tiles);
@@ -638,14 +725,21 @@ hb_status rebuild_tiles(hb_ctx* c, int TI, int TJ) {
   HB_CUDA(c, cudaMemcpy(c->d_tiles, tiles.data(), sizeof(int4) * n, cudaMemcpyHostToDevice));
   HB_CUDA(c, cudaMemcpy(c->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
   if (c->jobs_ok) {
-    // ghost jobs grouped by the tile owning the root, in destination order within a tile
-    std::vector<int> first_tile(c->blocks.size(), 0), tiles_i(c->blocks.size(), 1);
-    for (int q = n - 1; q >= 0; --q) first_tile[tiles[q].x] = q;
-    for (size_t b = 0; b < c->blocks.size(); ++b) tiles_i[b] = (c->blocks[b].n[0] + TI - 1) / TI;
+    // ghost jobs grouped by the tile owning the root, in destination order
+    // within a tile; owner[b][j * columns + i / TI] = tile of row j, column i
+    std::vector<std::vector<int>> owner(c->blocks.size());
+    std::vector<int> cols(c->blocks.size(), 1);
+    for (size_t b = 0; b < c->blocks.size(); ++b) {
+      cols[b] = (c->blocks[b].n[0] + TI - 1) / TI;
+      owner[b].assign((size_t)cols[b] * c->blocks[b].n[1], -1);
+    }
+    for (int q = 0; q < n; ++q)
+      for (int j = tiles[q].z; j < tiles[q].z + tiles[q].w; ++j)
+        owner[tiles[q].x][(size_t)j * cols[tiles[q].x] + tiles[q].y / TI] = q;
     std::vector<std::pair<int, int>> key(c->gjobs.size());
     for (size_t q = 0; q < c->gjobs.size(); ++q) {
       const auto& g = c->gjobs[q];
-      key[q] = {first_tile[g.root_blk] + (g.root_j / TJ) * tiles_i[g.root_blk] + g.root_i / TI, (int)q};
+      key[q] = {owner[g.root_blk][(size_t)g.root_j * cols[g.root_blk] + g.root_i / TI], (int)q};
     }
     std::stable_sort(key.begin(), key.end());
     std::vector<hbk::GhostJob> jobs(key.size());
@@ -905,7 +999,7 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
                       std::to_string(ctx->viscous) + "_c" + std::to_string(ctx->cases.size()) + "_n" +
                       std::to_string(ctx->total_cells) + "_b" + std::to_string(ctx->blocks.size()) + "_s";
     for (auto& ch : ctx->cases) key += std::to_string(ch.ns);
-    key += "_g1";   // drivers with the fused ghost fill
+    key += "_g2";   // drivers with the fused ghost fill and split wave tails
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -915,7 +1009,7 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
     int mm, aa, bb;
     if (ctx->dim == 2 && tune_lookup(ctx->tune_key, &mm, &aa, &bb)) { m = mm; a = aa; b = bb; }
     ctx->mode = m;
-    hb_status st = rebuild_tiles(ctx, a, b);
+    hb_status st = rebuild_tiles(ctx, a, b, m);
     if (st != HB_OK) return bad(st, ctx->err);
   }
   CK(cudaMalloc(&ctx->d_err, sizeof(int)));
@@ -1116,6 +1210,7 @@ hb_status persist_chunk(hb_ctx* c, T* U, int K, cudaStream_t s) {
     }
   }
   p.fused = c->fused() ? 1 : 0;
+  p.ns_max = c->ns_max;
   for (int pass = 0; pass < c->dim; ++pass) {
     hbk::HaloParams<T>& h = p.halo[pass];
     h.cases = (const CaseDev<T>*)c->d_cases;
@@ -1242,7 +1337,7 @@ hb_status autotune_impl(hb_ctx* c, const T* U, int iters, cudaStream_t s) {
   for (int m = 0; m < 2 && st == HB_OK; ++m)
     for (int q = 0; q < 3 && st == HB_OK; ++q) {
       if (m == 1 && !hbk::persist_available<T>(shapes[q][0], shapes[q][1])) continue;
-      if ((st = rebuild_tiles(c, shapes[q][0], shapes[q][1])) != HB_OK) break;
+      if ((st = rebuild_tiles(c, shapes[q][0], shapes[q][1], m)) != HB_OK) break;
       c->mode = m;
       cudaMemcpyAsync(tmp, U, c->tsize * c->state_size, cudaMemcpyDeviceToDevice, s);
       if ((st = rk_smooth_impl<T>(c, (T*)tmp, iters, nullptr, s)) != HB_OK) break;   // warm-up, graphs
@@ -1259,7 +1354,7 @@ hb_status autotune_impl(hb_ctx* c, const T* U, int iters, cudaStream_t s) {
   cudaStreamSynchronize(s);
   cudaFree(tmp);
   if (st != HB_OK) return st;
-  st = rebuild_tiles(c, bi, bj);
+  st = rebuild_tiles(c, bi, bj, bm);
   c->mode = bm;
   if (st == HB_OK) tune_store(c->tune_key, bm, bi, bj);
   return st;
@@ -1453,7 +1548,7 @@ hb_status hb_set_tuning(hb_ctx* ctx, int mode, int TI, int TJ) {
   const bool pok = ctx->prec == HB_FP32 ? hbk::persist_available<float>(TI, TJ)
                                         : hbk::persist_available<double>(TI, TJ);
   if (mode == 1 && !pok) return fail(ctx, HB_ERR_UNSUPPORTED, "persistent driver not built for this shape");
-  hb_status st = rebuild_tiles(ctx, TI, TJ);
+  hb_status st = rebuild_tiles(ctx, TI, TJ, mode);
   if (st != HB_OK) return st;
   ctx->mode = mode;
   ctx->halo_phases = phases;

@@ -145,6 +145,7 @@ struct PersistParams {
   long long timeout_ns;     // barrier wait limit
   int skip_cta;             // test hook: this CTA does not arrive at the first barrier (-1: none)
   int fused;                // 1: the stages fill the halos of their output (no halo phases)
+  int ns_max;               // largest snapshot count of the cases (sizes the shared memory)
 };
 
 // launchers (defined per precision in hb_kernels_f32.cu / hb_kernels_f64.cu)
@@ -158,8 +159,10 @@ cudaError_t launch_init(const CaseDev<T>* cases, const BlockDev* blocks, int nbl
                         const int64_t* block_noff, cudaStream_t s);
 template <typename T>
 cudaError_t launch_forces(const ForceParams<T>& p, cudaStream_t s);
+
+// SMs x resident CTAs of the RK-stage tile kernel (one wave of tiles)
 template <typename T>
-cudaError_t stage_smem_bytes(int TI, int TJ, size_t* bytes);
+cudaError_t stage_slots(int ns, int viscous, int TI, int TJ, int* slots);
 
 template <typename T>
 cudaError_t launch_stage3d(const StageParams<T>& p, int ns, int viscous, int mode, cudaStream_t s);

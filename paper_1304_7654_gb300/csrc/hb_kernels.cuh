@@ -174,8 +174,12 @@ __device__ __forceinline__ void visc2d(const T* gL, const T* gR, T uL, T vL, T T
 }
 
 // shared-memory elements of one tile CTA
-__host__ __device__ constexpr size_t tile2d_smem_elems(int TI, int TJ, int NS) {
-  return (size_t)10 * (TI + 4) * (TJ + 4) + (size_t)6 * (TI + 2) * (TJ + 2) +
+// The snapshot loop of a tile is pipelined (primitives double-buffered)
+// where the extra shared memory keeps the occupancy: up to 7 snapshots.
+__host__ __device__ constexpr bool tile_pipelined(int NS) { return NS <= 7; }
+
+__host__ __device__ constexpr size_t tile2d_smem_elems(int TI, int TJ, int NS, bool pipe) {
+  return (size_t)(pipe ? 15 : 10) * (TI + 4) * (TJ + 4) + (size_t)6 * (TI + 2) * (TJ + 2) +
          (size_t)4 * ((TI + 1) * TJ + TI * (TJ + 1)) + (size_t)NS * 4 * TI * TJ + (size_t)NS * NS;
 }
 
@@ -348,7 +352,7 @@ __device__ __forceinline__ void fill_tile_ghosts(const StageParams<T>& P, int t,
 // MODE 0: R := residual.  MODE 1: RK stage update (+ norm partials if set).
 // The tile shape TI x TJ (TI a power of two) is a compile-time constant so that
 // every flat-index decomposition is a multiply-shift.
-template <typename T, int NS, bool VISC, int MODE, int TI, int TJ>
+template <typename T, int NS, bool VISC, int MODE, int TI, int TJ, bool PIPE>
 __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   constexpr int NV = 4;
   const int4 tl = P.tiles[t];
@@ -363,10 +367,17 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int P0 = B.P[0];
   const int n0 = B.n[0], n1 = B.n[1];
+  // own rows j0 .. je-1 (a row strip of a tile has fewer than TJ); the
+  // region and the gradient ring are only needed two and one rows beyond
+  const int je = j0 + tl.w;
+  const int NRt = RI * (tl.w + 4), NGt = GI * (tl.w + 2);
 
-  T* sW = sm;              // [4][NR] primitives rho, u, v, p
-  T* sT = sW + 4 * NR;     // [NR] temperature gamma p / rho
-  T* sIV = sT + NR;        // [NR] 1 / volume
+  // PIPE: primitives and temperature double-buffered over snapshots, so
+  // that the region of snapshot n+1 is staged while the faces of n run
+  constexpr int NB = PIPE ? 2 : 1;
+  T* sW = sm;              // [NB][4][NR] primitives rho, u, v, p
+  T* sT = sW + NB * 4 * NR;   // [NB][NR] temperature gamma p / rho
+  T* sIV = sT + NB * NR;   // [NR] 1 / volume
   T* sS = sIV + NR;        // [d*2+comp][NR] low-face vectors
   T* sG = sS + 4 * NR;     // [6][NG] gradients on the 1-cell ring
   T* sF = sG + 6 * NG;     // [NV][NF] face fluxes
@@ -380,7 +391,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   const bool moving = C->motion != 0;
 
   // ---- static geometry of the region (tile + 2-cell halo), once per stage
-  for (int r = tid; r < NR; r += nt) {
+  for (int r = tid; r < NRt; r += nt) {
     const int ri = r % RI, rj = r / RI;
     const int i = i0 - 2 + ri, j = j0 - 2 + rj;
     if (i <= n0 + 1 && j <= n1 + 1) {
@@ -402,127 +413,128 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
 
   const int ti = tid % TI, tj = tid / TI;
   const int ci = i0 + ti, cj = j0 + tj;
-  const bool own = (tid < NT) && ci < n0 && cj < n1;
+  const bool own = (tid < NT) && ci < n0 && cj < je;
   const int rown = (tj + 2) * RI + (ti + 2);
   const int64_t cown = (int64_t)(cj + 2) * P0 + (ci + 2);
 
-  for (int n = 0; n < NS; ++n) {
-    const Fr<T> f = frame_at(C, n);
-    __syncthreads();
-    // ---- primitives of the region at snapshot n
-    for (int r = tid; r < NR; r += nt) {
-      const int ri = r % RI, rj = r / RI;
-      const int i = i0 - 2 + ri, j = j0 - 2 + rj;
-      T w0 = T(1), w1 = T(0), w2 = T(0), w3 = T(1), tt = gam;
-      if (i <= n0 + 1 && j <= n1 + 1) {
-        const T* u = P.Uprev + B.off + (int64_t)n * NV * B.plane + (int64_t)(j + 2) * P0 + (i + 2);
-        const T rho = u[0], mx = u[B.plane], my = u[2 * B.plane], E = u[3 * B.plane];
-        const T ir = Ar<T>::rcp(rho);
-        w0 = rho;
-        w1 = mx * ir;
-        w2 = my * ir;
-        w3 = gm1 * (E - T(0.5) * rho * (w1 * w1 + w2 * w2));
-        tt = gam * w3 * ir;
-      }
-      sW[r] = w0;
-      sW[NR + r] = w1;
-      sW[2 * NR + r] = w2;
-      sW[3 * NR + r] = w3;
-      sT[r] = tt;
+  // primitives of region cell r at snapshot n into buffer b
+  auto stage_cell = [&](int r, int n, int b) {
+    const int ri = r % RI, rj = r / RI;
+    const int i = i0 - 2 + ri, j = j0 - 2 + rj;
+    T w0 = T(1), w1 = T(0), w2 = T(0), w3 = T(1), tt = gam;
+    if (i <= n0 + 1 && j <= n1 + 1) {
+      const T* u = P.Uprev + B.off + (int64_t)n * NV * B.plane + (int64_t)(j + 2) * P0 + (i + 2);
+      const T rho = u[0], mx = u[B.plane], my = u[2 * B.plane], E = u[3 * B.plane];
+      const T ir = Ar<T>::rcp(rho);
+      w0 = rho;
+      w1 = mx * ir;
+      w2 = my * ir;
+      w3 = gm1 * (E - T(0.5) * rho * (w1 * w1 + w2 * w2));
+      tt = gam * w3 * ir;
     }
-    __syncthreads();
-    // ---- Green-Gauss gradients of (u, v, T) on the 1-cell ring, written as
-    // sum (phi_nb - phi_c)/2 S over the closed cell (the faces sum to zero),
-    // which keeps the rounding of large face vectors out of small cells
-    if (VISC) {
-      for (int gq = tid; gq < NG; gq += nt) {
-        const int gi = gq % GI, gj = gq / GI;
-        const int r = (gj + 1) * RI + (gi + 1);
-        const T uc = sW[NR + r], vc = sW[2 * NR + r], Tc = sT[r];
-        T g[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-        const int nb[4] = {r - 1, r + 1, r - RI, r + RI};
-        const int fo[4] = {r, r + 1, r, r + RI};
+    T* W = sW + b * 4 * NR;
+    W[r] = w0;
+    W[NR + r] = w1;
+    W[2 * NR + r] = w2;
+    W[3 * NR + r] = w3;
+    sT[b * NR + r] = tt;
+  };
+
+  // Green-Gauss gradients of (u, v, T) at ring cell gq from buffer b, written
+  // as sum (phi_nb - phi_c)/2 S over the closed cell (the faces sum to zero),
+  // which keeps the rounding of large face vectors out of small cells
+  auto grad_cell = [&](int gq, const Fr<T>& f, int b) {
+    const T* W = sW + b * 4 * NR;
+    const T* TT = sT + b * NR;
+    const int gi = gq % GI, gj = gq / GI;
+    const int r = (gj + 1) * RI + (gi + 1);
+    const T uc = W[NR + r], vc = W[2 * NR + r], Tc = TT[r];
+    T g[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    const int nb[4] = {r - 1, r + 1, r - RI, r + RI};
+    const int fo[4] = {r, r + 1, r, r + RI};
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int d = k >> 1;
-          const T sg = (k & 1) ? T(0.5) : T(-0.5);
-          T sx, sy;
-          rotv(f, sS[(2 * d) * NR + fo[k]], sS[(2 * d + 1) * NR + fo[k]], sx, sy);
-          sx *= sg;
-          sy *= sg;
-          const int o = nb[k];
-          const T du = sW[NR + o] - uc, dv = sW[2 * NR + o] - vc, dT = sT[o] - Tc;
-          g[0] += du * sx; g[1] += du * sy;
-          g[2] += dv * sx; g[3] += dv * sy;
-          g[4] += dT * sx; g[5] += dT * sy;
-        }
-        const T iv = sIV[r];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) sG[q * NG + gq] = g[q] * iv;
-      }
-      __syncthreads();
-    }
-    // ---- every face of the tile once (faces no own cell uses are skipped)
-    for (int fq = tid; fq < NF; fq += nt) {
-      int rL, st, d, gLi, gRi, fi, fj;
-      if (fq < NFI) {
-        fi = fq % (TI + 1);
-        fj = fq / (TI + 1);
-        if (i0 + fi > n0 || j0 + fj >= n1) continue;
-        rL = (fj + 2) * RI + (fi + 1);
-        st = 1;
-        d = 0;
-        gLi = (fj + 1) * GI + fi;
-        gRi = gLi + 1;
-      } else {
-        const int g2 = fq - NFI;
-        fi = g2 % TI;
-        fj = g2 / TI;
-        if (i0 + fi >= n0 || j0 + fj > n1) continue;
-        rL = (fj + 1) * RI + (fi + 2);
-        st = RI;
-        d = 1;
-        gLi = fj * GI + fi + 1;
-        gRi = gLi + GI;
-      }
-      const int rR = rL + st;
-      // the face is the low face of cell R = (i0 + fi, j0 + fj) along d
-      const int64_t gR = B.goff + (int64_t)(j0 + fj + 2) * P0 + (i0 + fi + 2);
-      T WL[4], WR[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const T a = sW[q * NR + rL - st], b = sW[q * NR + rL], c = sW[q * NR + rR],
-                dd = sW[q * NR + rR + st];
-        WL[q] = b + T(0.5) * van_albada(b - a, c - b, eps);
-        WR[q] = c - T(0.5) * van_albada(c - b, dd - c, eps);
-      }
+    for (int k = 0; k < 4; ++k) {
+      const int d = k >> 1;
+      const T sg = (k & 1) ? T(0.5) : T(-0.5);
       T sx, sy;
-      rotv(f, sS[(2 * d) * NR + rR], sS[(2 * d + 1) * NR + rR], sx, sy);
-      T vgn = T(0);
-      if (moving) {
-        T xf, yf;
-        rotp(f, __ldg(P.g.q[G_XF + 3 * d] + gR), __ldg(P.g.q[G_XF + 3 * d + 1] + gR), xf, yf);
-        const T vgx = -f.thd * (yf - f.py), vgy = f.thd * (xf - f.px);
-        vgn = (vgx * sx + vgy * sy) * Ar<T>::rsq(sx * sx + sy * sy);
-      }
-      T F[4];
-      roe2d(WL, WR, sx, sy, vgn, gm1, gg1, ig1, efix, efrac, F);
-      if (VISC) {
-        T gl[6], gr[6];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) { gl[q] = sG[q * NG + gLi]; gr[q] = sG[q * NG + gRi]; }
-        T tx, ty;
-        rotv(f, __ldg(P.g.q[G_DC + 3 * d] + gR), __ldg(P.g.q[G_DC + 3 * d + 1] + gR), tx, ty);
-        T Fv[4];
-        visc2d(gl, gr, sW[NR + rL], sW[2 * NR + rL], sT[rL], sW[NR + rR], sW[2 * NR + rR], sT[rR], tx,
-               ty, sx, sy, mu, kap, Fv);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) F[q] -= Fv[q];
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) sF[q * NF + fq] = F[q];
+      rotv(f, sS[(2 * d) * NR + fo[k]], sS[(2 * d + 1) * NR + fo[k]], sx, sy);
+      sx *= sg;
+      sy *= sg;
+      const int o = nb[k];
+      const T du = W[NR + o] - uc, dv = W[2 * NR + o] - vc, dT = TT[o] - Tc;
+      g[0] += du * sx; g[1] += du * sy;
+      g[2] += dv * sx; g[3] += dv * sy;
+      g[4] += dT * sx; g[5] += dT * sy;
     }
-    __syncthreads();
+    const T iv = sIV[r];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sG[q * NG + gq] = g[q] * iv;
+  };
+
+  // one face of the tile from buffer b (faces no own cell uses are skipped)
+  auto face = [&](int fq, const Fr<T>& f, int b) {
+    const T* W = sW + b * 4 * NR;
+    const T* TT = sT + b * NR;
+    int rL, st, d, gLi, gRi, fi, fj;
+    if (fq < NFI) {
+      fi = fq % (TI + 1);
+      fj = fq / (TI + 1);
+      if (i0 + fi > n0 || j0 + fj >= je) return;
+      rL = (fj + 2) * RI + (fi + 1);
+      st = 1;
+      d = 0;
+      gLi = (fj + 1) * GI + fi;
+      gRi = gLi + 1;
+    } else {
+      const int g2 = fq - NFI;
+      fi = g2 % TI;
+      fj = g2 / TI;
+      if (i0 + fi >= n0 || j0 + fj > je) return;
+      rL = (fj + 1) * RI + (fi + 2);
+      st = RI;
+      d = 1;
+      gLi = fj * GI + fi + 1;
+      gRi = gLi + GI;
+    }
+    const int rR = rL + st;
+    // the face is the low face of cell R = (i0 + fi, j0 + fj) along d
+    const int64_t gR = B.goff + (int64_t)(j0 + fj + 2) * P0 + (i0 + fi + 2);
+    T WL[4], WR[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const T a = W[q * NR + rL - st], bb = W[q * NR + rL], c = W[q * NR + rR], dd = W[q * NR + rR + st];
+      WL[q] = bb + T(0.5) * van_albada(bb - a, c - bb, eps);
+      WR[q] = c - T(0.5) * van_albada(c - bb, dd - c, eps);
+    }
+    T sx, sy;
+    rotv(f, sS[(2 * d) * NR + rR], sS[(2 * d + 1) * NR + rR], sx, sy);
+    T vgn = T(0);
+    if (moving) {
+      T xf, yf;
+      rotp(f, __ldg(P.g.q[G_XF + 3 * d] + gR), __ldg(P.g.q[G_XF + 3 * d + 1] + gR), xf, yf);
+      const T vgx = -f.thd * (yf - f.py), vgy = f.thd * (xf - f.px);
+      vgn = (vgx * sx + vgy * sy) * Ar<T>::rsq(sx * sx + sy * sy);
+    }
+    T F[4];
+    roe2d(WL, WR, sx, sy, vgn, gm1, gg1, ig1, efix, efrac, F);
+    if (VISC) {
+      T gl[6], gr[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) { gl[q] = sG[q * NG + gLi]; gr[q] = sG[q * NG + gRi]; }
+      T tx, ty;
+      rotv(f, __ldg(P.g.q[G_DC + 3 * d] + gR), __ldg(P.g.q[G_DC + 3 * d + 1] + gR), tx, ty);
+      T Fv[4];
+      visc2d(gl, gr, W[NR + rL], W[2 * NR + rL], TT[rL], W[NR + rR], W[2 * NR + rR], TT[rR], tx, ty, sx,
+             sy, mu, kap, Fv);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) F[q] -= Fv[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sF[q * NF + fq] = F[q];
+  };
+
+  // flux balance of the own cell at snapshot n from the face fluxes
+  auto accumulate = [&](int n) {
     if (own) {
       const int fi0 = tj * (TI + 1) + ti;
       const int fj0 = NFI + tj * TI + ti;
@@ -531,6 +543,53 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
         sAcc[(n * NV + q) * NT + tid] =
             (sF[q * NF + fi0 + 1] - sF[q * NF + fi0]) + (sF[q * NF + fj0 + TI] - sF[q * NF + fj0]);
     }
+  };
+
+  if constexpr (PIPE) {
+    // prologue: snapshot 0 staged (and its gradients); then per snapshot two
+    // phases: (A) faces of n + staging of n+1, (B) balance of n + gradients
+    // of n+1
+    for (int r = tid; r < NRt; r += nt) stage_cell(r, 0, 0);
+    __syncthreads();
+    if (VISC) {
+      const Fr<T> f0 = frame_at(C, 0);
+      for (int gq = tid; gq < NGt; gq += nt) grad_cell(gq, f0, 0);
+      __syncthreads();
+    }
+    for (int n = 0; n < NS; ++n) {
+      const int b = n & 1;
+      const bool next = n + 1 < NS;
+      const Fr<T> f = frame_at(C, n);
+      // one round-robin over faces then region cells: a thread with one face
+      // fewer takes a region cell first
+      int w = tid;
+      for (; w < NF; w += nt) face(w, f, b);
+      if (next)
+        for (w -= NF; w < NRt; w += nt) stage_cell(w, n + 1, b ^ 1);
+      __syncthreads();
+      accumulate(n);
+      if (VISC && next) {
+        const Fr<T> f1 = frame_at(C, n + 1);
+        for (int gq = tid; gq < NGt; gq += nt) grad_cell(gq, f1, b ^ 1);
+      }
+      __syncthreads();
+    }
+  } else {
+    // per snapshot: staging, gradients, faces, balance; the staging of n+1
+    // needs no barrier after the balance of n (which reads only the fluxes)
+    for (int n = 0; n < NS; ++n) {
+      const Fr<T> f = frame_at(C, n);
+      for (int r = tid; r < NRt; r += nt) stage_cell(r, n, 0);
+      __syncthreads();
+      if (VISC) {
+        for (int gq = tid; gq < NGt; gq += nt) grad_cell(gq, f, 0);
+        __syncthreads();
+      }
+      for (int fq = tid; fq < NF; fq += nt) face(fq, f, 0);
+      __syncthreads();
+      accumulate(n);
+    }
+    __syncthreads();
   }
 
   // ---- epilogue: HB source, residual or RK update, norm partials
@@ -624,7 +683,7 @@ template <typename T, int NS, bool VISC, int MODE, int TI, int TJ>
 __global__ void __launch_bounds__(TI * TJ, (sizeof(T) == 4 ? 3 : 1) * (MAXNT / (TI * TJ)))
     tile2d_kernel(StageParams<T> P) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  tile2d<T, NS, VISC, MODE, TI, TJ>(P, blockIdx.x, reinterpret_cast<T*>(smraw));
+  tile2d<T, NS, VISC, MODE, TI, TJ, tile_pipelined(NS)>(P, blockIdx.x, reinterpret_cast<T*>(smraw));
 }
 
 // tile shapes built into the library (index = StageParams shape id)

@@ -62,7 +62,10 @@ def test_batch_equals_cases_run_alone(prec):
             same = torch.equal(ctx.to_compact(U), ctx.to_compact(Ub[a:e].clone()))
             if mode == 1:
                 assert same, (k, mode)           # same kernel: bitwise
-                assert torch.equal(n1, nb[:, k])
+                # the norms sum FP64 per-tile partials; the batch and the lone
+                # case split their last wave into different row strips, so
+                # the partials group differently: equal to FP64 rounding
+                assert np.allclose(n1.cpu().numpy(), nb[:, k].cpu().numpy(), rtol=1e-12, atol=0), k
             else:   # a separately compiled kernel: equal to rounding
                 a_, b_ = ctx.to_compact(U), ctx.to_compact(Ub[a:e].clone())
                 assert (a_ - b_).abs().max() <= 2e-6 * b_.abs().max(), (k, (a_ - b_).abs().max())
@@ -85,22 +88,25 @@ def test_batch_fp64_matches_oracle_per_case():
 
 
 def test_tile_shape_and_driver_do_not_change_the_state():
-    # each face is computed once from the same inputs whatever the tile shape:
-    # bitwise equal within a driver; the two drivers are separately compiled
-    # kernels and agree to rounding
+    # each face is computed once from the same inputs whatever the tile shape
+    # or row-strip split: a rerun is bitwise equal; other tile shapes and the
+    # other driver are separately compiled kernels (the compiler may fuse a
+    # multiply-add in one and not the other) and agree to FP32 rounding
     c = C.ns_ogrid8(128, 24, n_harm=2)
-    ref = {}
+    ref = None
     for mode, TI, TJ in [(0, 32, 8), (0, 32, 4), (0, 16, 8), (1, 32, 8), (1, 32, 4), (1, 16, 8)]:
-        ctx = hb.HBContext(c, "fp32")
-        ctx.set_tuning(mode, TI, TJ)
-        U = ctx.new_state()
-        ctx.init_state(U, torch.as_tensor(C.noise(c), device="cuda"), 0.01)
-        ctx.rk_smooth(U, 3)
-        if mode not in ref:
-            ref[mode] = U.clone()
-        else:
-            assert torch.equal(U, ref[mode]), (mode, TI, TJ)
-    assert (ref[0] - ref[1]).abs().max() <= 2e-6 * ref[0].abs().max()
+        runs = []
+        for _ in range(2):
+            ctx = hb.HBContext(c, "fp32")
+            ctx.set_tuning(mode, TI, TJ)
+            U = ctx.new_state()
+            ctx.init_state(U, torch.as_tensor(C.noise(c), device="cuda"), 0.01)
+            ctx.rk_smooth(U, 3)
+            runs.append(U)
+        assert torch.equal(runs[0], runs[1]), (mode, TI, TJ)
+        if ref is None:
+            ref = runs[0]
+        assert (runs[0] - ref).abs().max() <= 2e-6 * ref.abs().max(), (mode, TI, TJ)
 
 
 def test_barrier_timeout_is_reported_and_context_recovers():

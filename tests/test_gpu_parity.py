@@ -195,6 +195,20 @@ def test_full_size_ns_ogrid8_sampled_residual(prec):
     assert err[te].max() < (TOL[prec] if prec == "fp64" else 2e-4), err[te].max()
 
 
+def test_full_size_ns_ogrid8_stays_finite_over_600_iterations():
+    # the measured workload itself: the RK smoother must stay finite over at
+    # least as many iterations as a benchmark run takes (with CFL 1.5 this
+    # O-grid diverged at iteration 68, identically in FP32 and FP64)
+    cs = C.ns_ogrid8()
+    ctx = hb.HBContext(cs, "fp32")
+    U = ctx.new_state()
+    ctx.init_state(U, torch.as_tensor(C.noise(cs), device="cuda"), 0.01)
+    n = ctx.rk_smooth(U, 600).cpu().numpy()
+    assert ctx.sync_status() == hb.HB_OK
+    assert np.isfinite(n).all()
+    assert n[-1].max() < 10 * n[0].max()
+
+
 def test_rk_is_bitwise_deterministic_and_graph_equals_direct():
     cs = C.ns_ogrid8(128, 24, n_harm=3)
     o, U, ctx, Ug = _setup(cs, "fp64")

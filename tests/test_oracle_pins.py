@@ -484,13 +484,15 @@ def test_adjoint_columns_dual_match_central_differences():
     cells = C.sample_cells(cs, 6, 11)
     cols = np.array([[*c, v, n] for c in cells for v in range(cs.nv) for n in (0, cs.n_snap - 1)])
     exact = o.adjoint_columns(U, psi, 0.7, cols, mode=0)
-    fd = o.adjoint_columns(U, psi, 0.7, cols, mode=1, h=1e-6)
+    # central differences carry an O(h^2) truncation error (measured: x100 per
+    # decade of h); h = 1e-7 keeps it near 1e-8 relative, above FP64 rounding
+    fd = o.adjoint_columns(U, psi, 0.7, cols, mode=1, h=1e-7)
     scale = np.abs(exact).max()
     assert np.max(np.abs(exact - fd)) < 1e-6 * scale
     # wall-adjacent cells see the functional
     wall = np.array([[0, 3, 0, 0, v, 0] for v in range(cs.nv)])
     ej = o.adjoint_columns(U, psi * 0, 1.0, wall, mode=0)
-    fj = o.adjoint_columns(U, psi * 0, 1.0, wall, mode=1, h=1e-6)
+    fj = o.adjoint_columns(U, psi * 0, 1.0, wall, mode=1, h=1e-7)
     assert np.abs(ej).max() > 0
     assert np.max(np.abs(ej - fj)) < 1e-6 * np.abs(ej).max()
 
