@@ -463,7 +463,7 @@ hb_status resolve_ghost_jobs(hb_ctx* ctx, const Tables& T, const int* bc_index) 
         g.root_blk = x.blk;
         g.root_i = x.cell % R.P[0] - 2;
         g.root_j = x.cell / R.P[0] - 2;
-        g.job = hbk::GhostJob{b, c, x.cell, x.nops, {x.op[0], x.op[1], x.op[2]}, 0};
+        g.job = hbk::GhostJob{b, c, x.cell, x.nops, {x.op[0], x.op[1], x.op[2]}, x.blk};
         ctx->gjobs.push_back(g);
       }
   }
@@ -1078,8 +1078,30 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
 }
 
 // ------------------------------------------------------------ launches --
+// every ghost cell of dst from the interior of src in one launch (2D)
+template <typename T>
+hb_status ghost_fill(hb_ctx* c, const T* src, T* dst, cudaStream_t s) {
+  hbk::GhostFillParams<T> p;
+  p.cases = (const CaseDev<T>*)c->d_cases;
+  p.blocks = c->d_blocks;
+  p.g = geo_of<T>(c);
+  p.src = src;
+  p.dst = dst;
+  p.jobs = c->d_jobs;
+  p.njobs = (int)c->gjobs.size();
+  p.bcs = c->d_job_bcs;
+  p.ns_max = c->ns_max;
+  if (p.njobs == 0) return HB_OK;
+  TimedScope ts(c, 1, s);
+  HB_CUDA(c, hbk::launch_ghost_fill<T>(p, s));
+  return HB_OK;
+}
+
+// halo fill in place: 2D one launch over the resolved ghost chains, 3D the
+// pass-ordered cut copies and boundary records (one launch per pass)
 template <typename T>
 hb_status halos(hb_ctx* c, T* U, cudaStream_t s) {
+  if (c->jobs_ok) return ghost_fill<T>(c, U, U, s);
   hbk::HaloParams<T> p;
   p.cases = (const CaseDev<T>*)c->d_cases;
   p.blocks = c->d_blocks;
@@ -1361,26 +1383,34 @@ hb_status autotune_impl(hb_ctx* c, const T* U, int iters, cudaStream_t s) {
 }
 
 template <typename T>
-hb_status forces_filled(hb_ctx* c, const T* W, double* coef, double* J, cudaStream_t s);
+hb_status forces_filled(hb_ctx* c, const T* W, const T* G, double* coef, double* J, cudaStream_t s);
 
+// U is the caller's (not written): 2D fills the ghosts into the workspace and
+// the force kernel reads interior cells from U and ghosts from there
 template <typename T>
 hb_status forces_impl(hb_ctx* c, const T* U, double* coef, double* J, cudaStream_t s) {
   T* W = (T*)c->d_A;
+  if (c->jobs_ok) {
+    hb_status st = ghost_fill<T>(c, U, W, s);
+    if (st != HB_OK) return st;
+    return forces_filled<T>(c, U, W, coef, J, s);
+  }
   c->n_launch++;
   HB_CUDA(c, hbk::launch_copy(W, U, (int64_t)c->tsize * c->state_size, s));
   hb_status st = halos<T>(c, W, s);
   if (st != HB_OK) return st;
-  return forces_filled<T>(c, W, coef, J, s);
+  return forces_filled<T>(c, W, nullptr, coef, J, s);
 }
 
-// forces of a state whose ghosts are filled
+// forces of a state W whose ghosts are filled (in W, or in G when not null)
 template <typename T>
-hb_status forces_filled(hb_ctx* c, const T* W, double* coef, double* J, cudaStream_t s) {
+hb_status forces_filled(hb_ctx* c, const T* W, const T* G, double* coef, double* J, cudaStream_t s) {
   hbk::ForceParams<T> p;
   p.cases = (const CaseDev<T>*)c->d_cases;
   p.blocks = c->d_blocks;
   p.g = geo_of<T>(c);
   p.U = W;
+  p.G = G;
   p.walls = c->d_walls;
   p.nwall = c->nwall;
   p.ns = c->cases[0].ns;
@@ -1526,7 +1556,7 @@ hb_status hb_adjoint_residual(hb_ctx* ctx, const void* U, const void* psi, doubl
   }
   ctx->n_launch += 3 + ctx->dim;
   HB_CUDA(ctx, hbk::launch_adjoint(p, gp, ctx->dim, (double*)r_adj, s));
-  if (J_dev) return forces_filled<double>(ctx, W, nullptr, J_dev, s);
+  if (J_dev) return forces_filled<double>(ctx, W, nullptr, nullptr, J_dev, s);
   return HB_OK;
 }
 

@@ -67,11 +67,27 @@ struct BcRec {
 // cell (root_cell, in the block of the tile that owns it).  Cut copies are the
 // identity and leave no op.  After an RK stage the tile that wrote the root
 // writes the ghost, so the next stage finds every halo filled.
-struct GhostJob { int dst_blk, dst_cell, root_cell, nops, op[3], pad; };
+struct GhostJob { int dst_blk, dst_cell, root_cell, nops, op[3], root_blk; };
+
 
 template <typename T>
 struct Geo {
   const T* q[G_NQ];
+};
+
+// one launch filling every ghost cell of dst from the interior cells of src
+// (src == dst: an in-place halo fill; the roots are never ghosts)
+template <typename T>
+struct GhostFillParams {
+  const CaseDev<T>* cases;
+  const BlockDev* blocks;
+  Geo<T> g;
+  const T* src;
+  T* dst;
+  const GhostJob* jobs;
+  int njobs;
+  const BcRec* bcs;
+  int ns_max;
 };
 
 template <typename T>
@@ -111,7 +127,8 @@ struct ForceParams {
   const CaseDev<T>* cases;
   const BlockDev* blocks;
   Geo<T> g;
-  const T* U;               // halos filled
+  const T* U;               // interior cells (and ghosts when G is null)
+  const T* G;               // ghost cells (same layout), or null
   const BcRec* walls;
   int nwall;
   int ns;
@@ -159,6 +176,8 @@ cudaError_t launch_init(const CaseDev<T>* cases, const BlockDev* blocks, int nbl
                         const int64_t* block_noff, cudaStream_t s);
 template <typename T>
 cudaError_t launch_forces(const ForceParams<T>& p, cudaStream_t s);
+template <typename T>
+cudaError_t launch_ghost_fill(const GhostFillParams<T>& p, cudaStream_t s);
 
 // SMs x resident CTAs of the RK-stage tile kernel (one wave of tiles)
 template <typename T>

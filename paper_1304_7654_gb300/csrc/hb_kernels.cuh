@@ -316,37 +316,59 @@ __device__ __forceinline__ void bc_map(const CaseDev<T>* C, const Geo<T>& g, con
   if (DIM == 2) Wg[3] = T(0);
 }
 
+// One 2D ghost cell at snapshot n: its root cell of src (in block R) taken
+// through the job's chain of boundary maps, written to dst.
+template <typename T>
+__device__ __forceinline__ void ghost_job(const CaseDev<T>* C, const Geo<T>& g, const BlockDev* blocks,
+                                          const BcRec* bcs, const GhostJob* J, const BlockDev& R, int n,
+                                          const T* src, T* dst) {
+  constexpr int NV = 4;
+  const T gm1 = C->gamma - T(1);
+  const T* s = src + R.off + (int64_t)n * NV * R.plane + J->root_cell;
+  T Q[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Q[v] = s[v * R.plane];
+  const int nops = J->nops;
+  for (int k = 0; k < nops; ++k) {
+    const BcRec& r = bcs[J->op[k]];
+    T Wi[5], Wg[5];
+    prim_of<T, 2>(Q, gm1, Wi);
+    bc_map<T, 2>(C, g, blocks[r.blk], r.type, r.p, r.sgn, r.fcell, n, Wi, Wg);
+    cons_of<T, 2>(Wg, gm1, Q);
+  }
+  const BlockDev& D = blocks[J->dst_blk];
+  T* d = dst + D.off + (int64_t)n * NV * D.plane + J->dst_cell;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) d[v * D.plane] = Q[v];
+}
+
 // Fused ghost fill after an RK stage: the ghost cells whose root is an own
 // cell of tile t, at every snapshot, from the stage output just written.
 template <typename T, int NS>
 __device__ __forceinline__ void fill_tile_ghosts(const StageParams<T>& P, int t, const BlockDev& B,
                                                  const CaseDev<T>* C) {
-  constexpr int NV = 4;
   const int2 jr = P.job_range[t];
   if (jr.y <= 0) return;
   __syncthreads();   // own-cell outputs of every thread of the CTA are visible
-  const T gm1 = C->gamma - T(1);
   const int nitem = jr.y * NS;
   for (int w = threadIdx.x; w < nitem; w += blockDim.x) {
     const int n = w / jr.y;
-    const GhostJob* J = P.jobs + jr.x + (w - n * jr.y);
-    const T* src = P.Unext + B.off + (int64_t)n * NV * B.plane + J->root_cell;
-    T Q[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Q[v] = src[v * B.plane];
-    const int nops = J->nops;
-    for (int k = 0; k < nops; ++k) {
-      const BcRec& r = P.job_bcs[J->op[k]];
-      T Wi[5], Wg[5];
-      prim_of<T, 2>(Q, gm1, Wi);
-      bc_map<T, 2>(C, P.g, P.blocks[r.blk], r.type, r.p, r.sgn, r.fcell, n, Wi, Wg);
-      cons_of<T, 2>(Wg, gm1, Q);
-    }
-    const BlockDev& D = P.blocks[J->dst_blk];
-    T* dst = P.Unext + D.off + (int64_t)n * NV * D.plane + J->dst_cell;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) dst[v * D.plane] = Q[v];
+    ghost_job<T>(C, P.g, P.blocks, P.job_bcs, P.jobs + jr.x + (w - n * jr.y), B, n, P.Unext, P.Unext);
   }
+}
+
+// Every 2D ghost cell in one launch: one item per (job, snapshot),
+// snapshot-major so that neighbouring threads write neighbouring ghosts.
+template <typename T>
+__global__ void ghost_fill_kernel(GhostFillParams<T> p) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (int64_t)p.njobs * p.ns_max) return;
+  const int n = (int)(gid / p.njobs), q = (int)(gid - (int64_t)n * p.njobs);
+  const GhostJob* J = p.jobs + q;
+  const BlockDev& R = p.blocks[J->root_blk];
+  const CaseDev<T>* C = p.cases + R.cs;
+  if (n >= C->ns) return;
+  ghost_job<T>(C, p.g, p.blocks, p.bcs, J, R, n, p.src, p.dst);
 }
 
 // MODE 0: R := residual.  MODE 1: RK stage update (+ norm partials if set).
@@ -771,15 +793,23 @@ __global__ void init_kernel(const CaseDev<T>* cases, const BlockDev* blocks, Geo
 
 // ----------------------------------------------------------------- forces --
 // Green-Gauss gradient of (u, v, T) at padded cell c from global memory (2D)
+// snapshot base of padded cell cc: Ub for interior cells, Gb for ghosts
+template <typename T>
+__device__ __forceinline__ const T* cell_src(const BlockDev& B, const T* Ub, const T* Gb, int cc) {
+  const int i = cc % B.P[0] - 2, j = cc / B.P[0] - 2;
+  return (i >= 0 && i < B.n[0] && j >= 0 && j < B.n[1]) ? Ub : Gb;
+}
+
 template <typename T>
 __device__ void grad_global2d(const BlockDev& B, const CaseDev<T>* C, const Geo<T>& g,
-                              const T* Ub, const Fr<T>& f, int c, T* out) {
+                              const T* Ub, const T* Gb, const Fr<T>& f, int c, T* out) {
   const T gam = C->gamma, gm1 = gam - T(1);
   auto prim = [&](int cc, T& u, T& v, T& Tt) {
-    const T rho = Ub[cc];
-    u = Ub[B.plane + cc] / rho;
-    v = Ub[2 * B.plane + cc] / rho;
-    const T p = gm1 * (Ub[3 * B.plane + cc] - T(0.5) * rho * (u * u + v * v));
+    const T* X = cell_src(B, Ub, Gb, cc);
+    const T rho = X[cc];
+    u = X[B.plane + cc] / rho;
+    v = X[2 * B.plane + cc] / rho;
+    const T p = gm1 * (X[3 * B.plane + cc] - T(0.5) * rho * (u * u + v * v));
     Tt = gam * p / rho;
   };
   T uc, vc, Tc;
@@ -816,6 +846,7 @@ __global__ void force_faces_kernel(ForceParams<T> p) {
   const Fr<T> f = frame_at(C, n);
   const T gam = C->gamma, gm1 = gam - T(1);
   const T* Ub = p.U + B.off + (int64_t)n * 4 * B.plane;
+  const T* Gb = (p.G ? p.G : p.U) + B.off + (int64_t)n * 4 * B.plane;
   const int64_t fc = B.goff + r.fcell;
   T sx, sy, xf, yf;
   rotv(f, p.g.q[G_S + 3 * r.p][fc], p.g.q[G_S + 3 * r.p + 1][fc], sx, sy);
@@ -829,15 +860,16 @@ __global__ void force_faces_kernel(ForceParams<T> p) {
   if (C->viscous) {
     const int cl = (r.sgn > 0) ? ic : gc, cr = (r.sgn > 0) ? gc : ic;
     T gL[6], gR[6];
-    grad_global2d(B, C, p.g, Ub, f, cl, gL);
-    grad_global2d(B, C, p.g, Ub, f, cr, gR);
+    grad_global2d(B, C, p.g, Ub, Gb, f, cl, gL);
+    grad_global2d(B, C, p.g, Ub, Gb, f, cr, gR);
     T tx, ty;   // centre difference x_R - x_L, stored with the high cell cr = cl + e_p
     rotv(f, p.g.q[G_DC + 3 * r.p][B.goff + cr], p.g.q[G_DC + 3 * r.p + 1][B.goff + cr], tx, ty);
     auto prim = [&](int cc, T& uu, T& vv, T& Tt) {
-      const T rr = Ub[cc];
-      uu = Ub[B.plane + cc] / rr;
-      vv = Ub[2 * B.plane + cc] / rr;
-      Tt = gam * gm1 * (Ub[3 * B.plane + cc] - T(0.5) * rr * (uu * uu + vv * vv)) / rr;
+      const T* X = cell_src(B, Ub, Gb, cc);
+      const T rr = X[cc];
+      uu = X[B.plane + cc] / rr;
+      vv = X[2 * B.plane + cc] / rr;
+      Tt = gam * gm1 * (X[3 * B.plane + cc] - T(0.5) * rr * (uu * uu + vv * vv)) / rr;
     };
     T uL, vL, TL, uR, vR, TR;
     prim(cl, uL, vL, TL);
