@@ -281,6 +281,7 @@ def run_ours(args):
     batch = run_batch(args, dev) if not args.no_batch else None
     adj = adjoint_ratio(dev) if not args.no_adjoint else None
     box = run_box3d(args, dev) if not args.no_batch else None
+    shapes = run_paper_shapes(args, dev) if not args.no_batch else None
 
     # e2e: host buffers in pinned memory, H2D of the state and D2H of the
     # step's results (norms, force coefficients, J) inside the timed region
@@ -360,6 +361,7 @@ def run_ours(args):
             "batched_fp32": batch,
             "adjoint": adj,
             "box3d_fp32": box,
+            "paper_shapes_fp32": shapes,
             "kernel_share": {"tile_ms": r32["tile_ms"], "halo_ms": r32["halo_ms"], "step_ms_total": ms32},
             "status": [r32["status"], r64["status"]]}
     if not args.no_cpu_baseline and ws == 1:
@@ -397,6 +399,56 @@ def run_batch(args, dev):
             "cell_snapshots": int(sum(c.n_cells * c.n_snap for c in cases)),
             **_tuning_desc(mode, TI, TJ),
             "status": _checked_status(ctx, "batched FP32")}
+
+
+def run_paper_shapes(args, dev):
+    """The shapes of the paper's two test cases (Sec. 4.1), FP32, one launch
+    per phase (N_s above 9: HB source from its own launch): TC1-like, 512
+    blocks of 32x16 = 262,144 cells, 31 snapshots, pitching; TC2-like, 2048
+    blocks of 64x32 = 4,194,304 cells, 17 snapshots, yawing inflow.  Inputs
+    (~0.7 and ~1.4 GB per state) exceed L2."""
+    import numpy as np
+    import torch
+    from paper_1304_7654_gb300 import cases as C
+    from paper_1304_7654_gb300 import hb
+    out = {}
+    for name, make in (("tc1_like", C.paper_tc1), ("tc2_like", C.paper_tc2)):
+        cs = make()
+        ctx = hb.HBContext(cs, "fp32")
+        U = ctx.new_state(dev)
+        ctx.init_state(U, torch.as_tensor(C.noise(cs), device=dev), 0.01)
+        mode, TI, TJ = ctx.autotune(U, iters=1)
+        ctx.rk_smooth(U, 3, norms=False)
+        steps = max(3, min(args.steps, 20))
+        torch.cuda.synchronize()
+        ctx.kernel_stats(0, reset=True)
+        ctx.set_timing(True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            ctx.rk_smooth(U, 1, norms=False)
+        b.record()
+        torch.cuda.synchronize()
+        tile_ms, tile_n = ctx.kernel_stats(0)
+        aux_ms, aux_n = ctx.kernel_stats(1)
+        ctx.set_timing(False)
+        ms = a.elapsed_time(b) / steps
+        units = cs.n_cells * cs.n_snap * 4
+        tl = tile_ms / max(1, tile_n)
+        bpu = algorithmic_bytes_per_unit(cs.nv, 4, cs.motion != 0, cs.viscous, cs.n_snap)
+        peaks, _ = _peaks()
+        out[name] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_iteration": ms, "iterations": steps,
+                     "cells": cs.n_cells, "blocks": len(cs.blocks), "n_snap": cs.n_snap,
+                     **_tuning_desc(mode, TI, TJ),
+                     "tile_kernel": {"launch_ms": tl,
+                                     "algorithmic_GBs": bpu * cs.n_cells * cs.n_snap / (tl * 1e-3) / 1e9,
+                                     "frac_of_measured_hbm": bpu * cs.n_cells * cs.n_snap / (tl * 1e-3) / 1e9
+                                     / peaks["hbm_gbs"]},
+                     "aux_launches_ms_per_iteration": aux_ms / steps,
+                     "status": _checked_status(ctx, name)}
+        del ctx, U
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_box3d(args, dev):

@@ -59,8 +59,14 @@ typedef enum { HB_BC_FARFIELD = 1, HB_BC_SLIP = 2, HB_BC_NOSLIP = 3 } hb_bc_type
 typedef enum { HB_MOTION_NONE = 0, HB_MOTION_PITCH = 1 } hb_motion;
 typedef enum { HB_UBC_NONE = 0, HB_UBC_INLET_ANGLE = 1, HB_UBC_GUST = 2 } hb_unsteady_bc;
 
-/* Largest supported number of harmonics N_H (snapshots 2*N_H+1). */
-#define HB_MAX_HARMONICS 4
+/* Largest supported number of harmonics N_H (snapshots 2*N_H+1): 15, i.e.
+ * the 31 snapshots of the paper's first test case (Sec. 4.1).  Up to
+ * HB_MAX_STATIC_HARMONICS the tile kernel is specialised on the snapshot
+ * count and forms the HB source itself; above, a separate launch forms
+ * H = V omega D U first, and 3D contexts and the persistent driver are not
+ * available (HB_ERR_UNSUPPORTED). */
+#define HB_MAX_HARMONICS 15
+#define HB_MAX_STATIC_HARMONICS 4
 
 /* One structured block of ni x nj (x nk) cells.  `nodes` is host memory, read
  * only during hb_create: (ni+5)*(nj+5)[*(nk+5)] points with `dim` coordinates
@@ -100,7 +106,7 @@ typedef struct {
 typedef struct {
   int dim;                    /* 2 or 3; 3D runs one launch per phase with 8x8x4 tiles and has no
                                  force integration or adjoint (HB_ERR_UNSUPPORTED) */
-  int n_harm;                 /* N_H, 0 .. HB_MAX_HARMONICS */
+  int n_harm;                 /* N_H, 0 .. HB_MAX_HARMONICS (3D: .. HB_MAX_STATIC_HARMONICS) */
   double mach, reynolds, prandtl, gamma;
   double alpha0_deg;          /* mean incidence of the freestream */
   double omega;               /* fundamental angular frequency */

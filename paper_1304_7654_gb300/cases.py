@@ -339,6 +339,32 @@ def ns_ogrid8(ni=1280, nj=192, n_harm=3, viscous=True, **kw):
                  specs=ogrid8_specs(ni, nj), name="ns_ogrid8", **kw)
 
 
+def block_lattice(ni: int, nj: int, bi: int, bj: int):
+    """ni x nj cells cut into a lattice of bi x bj blocks."""
+    return [BlockSpec((i, j), (i + bi, j + bj)) for j in range(0, nj, bj) for i in range(0, ni, bi)]
+
+
+def paper_tc1(ni=1024, nj=256, n_harm=15, **kw):
+    """Shape of the paper's first test case (Sec. 4.1): 512 blocks of 32x16
+    cells (262,144 cells), 31 snapshots; a pitching wing section, inviscid
+    (the synthetic stand-in for the heaving and pitching energy-extraction
+    wing, whose grid is not available)."""
+    return ogrid(ni=ni, nj=nj, n_harm=n_harm, viscous=False, specs=block_lattice(ni, nj, ni // 32, nj // 16),
+                 name="paper_tc1", seed=41, **kw)
+
+
+def paper_tc2(ni=4096, nj=1024, n_harm=8, **kw):
+    """Shape of the paper's second test case (Sec. 4.1): 2048 blocks of
+    64x32 cells (4,194,304 cells), 17 snapshots; an inviscid wing section in a
+    periodically yawing stream (the synthetic stand-in for the wind-turbine
+    blade section in yawed wind: fixed grid, inflow angle varying at the
+    fundamental frequency)."""
+    cs = ogrid(ni=ni, nj=nj, n_harm=n_harm, viscous=False, pitch_deg=0.0,
+               specs=block_lattice(ni, nj, ni // 64, nj // 32), name="paper_tc2", seed=42, **kw)
+    cs.ubc, cs.ubc_amp = UBC_INLET_ANGLE, 2.0
+    return cs
+
+
 def adjoint_ogrid4(ni=512, nj=256, n_harm=4, **kw):
     """Adjoint workload: 4 blocks 96/160/128/128 of 512 in i, laminar, N_H = 4."""
     widths = np.round(np.cumsum([0, 96, 160, 128, 128]) * ni / 512).astype(int)

@@ -86,6 +86,14 @@ struct hb_ctx {
   int2* d_job_range = nullptr;   // [job_range_cap]
   int job_range_cap = 0;
   BcRec* d_job_bcs = nullptr;
+  // large-N_s cases (N_s above the kernel's compile-time counts): the HB
+  // source H = V omega D U is formed by its own launch over these chunks
+  int2* d_chunks = nullptr;      // (block, first padded cell) of 128-cell chunks, grouped by N_s
+  int nchunks = 0;
+  struct SrcGroup { int ns, first, count; std::vector<double> D; };
+  std::vector<SrcGroup> src_groups;
+  void* d_H = nullptr;
+  bool large_ns() const { return nchunks > 0; }
   int n_bodies = 0;
   void* d_A = nullptr;          // RK ping-pong and residual scratch
   void* d_B = nullptr;
@@ -562,6 +570,8 @@ void free_ctx(hb_ctx* c) {
   cudaFree(c->d_jobs);
   cudaFree(c->d_job_range);
   cudaFree(c->d_job_bcs);
+  cudaFree(c->d_chunks);
+  cudaFree(c->d_H);
   cudaFree(c->d_A);
   cudaFree(c->d_B);
   cudaFree(c->d_partials);
@@ -841,6 +851,8 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
       return bad(HB_ERR_INVALID_ARG, "batched cases must share dim, precision and viscosity");
     if (d.n_harm < 0) return bad(HB_ERR_INVALID_ARG, "n_harm < 0");
     if (d.n_harm > HB_MAX_HARMONICS) return bad(HB_ERR_UNSUPPORTED, "n_harm above HB_MAX_HARMONICS");
+    if (d.dim == 3 && d.n_harm > HB_MAX_STATIC_HARMONICS)
+      return bad(HB_ERR_UNSUPPORTED, "3D contexts support n_harm up to HB_MAX_STATIC_HARMONICS");
     if (d.n_blocks <= 0 || !d.blocks) return bad(HB_ERR_INVALID_ARG, "no blocks");
     if ((d.n_cuts > 0 && !d.cuts) || (d.n_bcs > 0 && !d.bcs) || d.n_cuts < 0 || d.n_bcs < 0)
       return bad(HB_ERR_INVALID_ARG, "null table");
@@ -969,6 +981,36 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
     }
     ctx->jobs_ok = true;
   }
+  {   // chunks of the large-N_s blocks for the HB source launches, one group per N_s
+    std::vector<int2> ch;
+    for (int ns = 2 * HB_MAX_STATIC_HARMONICS + 3; ns <= 2 * HB_MAX_HARMONICS + 1; ns += 2) {
+      hb_ctx::SrcGroup grp;
+      grp.ns = ns;
+      grp.first = (int)ch.size();
+      for (const CaseHost& cs : ctx->cases) {
+        if (cs.ns != ns) continue;
+        for (int b = cs.block0; b < cs.block0 + cs.nblocks; ++b)
+          for (int64_t c0 = 0; c0 < ctx->blocks[b].plane; c0 += 128) ch.push_back(make_int2(b, (int)c0));
+      }
+      grp.count = (int)ch.size() - grp.first;
+      if (grp.count == 0) continue;
+      grp.D.assign((size_t)ns * ns, 0.0);
+      for (int n = 0; n < ns; ++n)
+        for (int m = 0; m < ns; ++m)
+          if (n != m) {
+            const int k = n - m;
+            grp.D[(size_t)n * ns + m] = 0.5 * ((k % 2 == 0) ? 1.0 : -1.0) / std::sin(M_PI * (double)k / (double)ns);
+          }
+      ctx->src_groups.push_back(grp);
+    }
+    ctx->nchunks = (int)ch.size();
+    if (ctx->nchunks) {
+      CK(cudaMalloc(&ctx->d_chunks, sizeof(int2) * ch.size()));
+      CK(cudaMemcpy(ctx->d_chunks, ch.data(), sizeof(int2) * ch.size(), cudaMemcpyHostToDevice));
+      CK(cudaMalloc(&ctx->d_H, ts * ctx->state_size));
+      CK(cudaMemset(ctx->d_H, 0, ts * ctx->state_size));
+    }
+  }
   ctx->nwall = (int)Tb.walls.size();
   if (ctx->nwall) {
     CK(cudaMalloc(&ctx->d_walls, sizeof(BcRec) * ctx->nwall));
@@ -1005,7 +1047,8 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     key += "_sm" + std::to_string(sms);
     ctx->tune_key = key.substr(0, 500);
-    int m = (ctx->cases.size() > 1 && ctx->prec == HB_FP32 && ctx->dim == 2) ? 1 : 0, a = 32, b = 8;
+    int m = (ctx->cases.size() > 1 && ctx->prec == HB_FP32 && ctx->dim == 2 && !ctx->large_ns()) ? 1 : 0;
+    int a = 32, b = 8;
     int mm, aa, bb;
     if (ctx->dim == 2 && tune_lookup(ctx->tune_key, &mm, &aa, &bb)) { m = mm; a = aa; b = bb; }
     ctx->mode = m;
@@ -1153,6 +1196,18 @@ hb_status stage_all(hb_ctx* c, hbk::StageParams<T> p, int mode, cudaStream_t s) 
   return HB_OK;
 }
 
+// H = V omega D W for the large-N_s cases
+template <typename T>
+hb_status hb_source(hb_ctx* c, const T* W, cudaStream_t s) {
+  for (const auto& grp : c->src_groups) {
+    TimedScope ts(c, 1, s);
+    HB_CUDA(c, hbk::launch_hb_source<T>((const CaseDev<T>*)c->d_cases, c->d_blocks, geo_of<T>(c),
+                                        c->d_chunks + grp.first, grp.count, c->nv, grp.ns, grp.D.data(), W,
+                                        (T*)c->d_H, s));
+  }
+  return HB_OK;
+}
+
 template <typename T>
 hb_status residual_impl(hb_ctx* c, const T* U, T* R, cudaStream_t s) {
   T* W = (T*)c->d_A;
@@ -1163,6 +1218,9 @@ hb_status residual_impl(hb_ctx* c, const T* U, T* R, cudaStream_t s) {
   auto p = stage_params<T>(c);
   p.Uprev = W;
   p.R = R;
+  st = hb_source<T>(c, W, s);
+  if (st != HB_OK) return st;
+  p.H = (const T*)c->d_H;
   return stage_all<T>(c, p, 0, s);
 }
 
@@ -1189,6 +1247,9 @@ hb_status rk_iteration(hb_ctx* c, T* U, double* norm_out, cudaStream_t s) {
     p.Unext = out[st];
     p.alpha = (T)alpha[st];
     p.partials = (st == 0) ? c->d_partials : nullptr;
+    r = hb_source<T>(c, in[st], s);
+    if (r != HB_OK) return r;
+    p.H = (const T*)c->d_H;
     r = stage_all<T>(c, p, 1, s);
     if (r != HB_OK) return r;
     if (st == 0) {
@@ -1358,7 +1419,7 @@ hb_status autotune_impl(hb_ctx* c, const T* U, int iters, cudaStream_t s) {
   const int shapes[3][2] = {{32, 8}, {32, 4}, {16, 8}};
   for (int m = 0; m < 2 && st == HB_OK; ++m)
     for (int q = 0; q < 3 && st == HB_OK; ++q) {
-      if (m == 1 && !hbk::persist_available<T>(shapes[q][0], shapes[q][1])) continue;
+      if (m == 1 && (c->large_ns() || !hbk::persist_available<T>(shapes[q][0], shapes[q][1]))) continue;
       if ((st = rebuild_tiles(c, shapes[q][0], shapes[q][1], m)) != HB_OK) break;
       c->mode = m;
       cudaMemcpyAsync(tmp, U, c->tsize * c->state_size, cudaMemcpyDeviceToDevice, s);
@@ -1578,6 +1639,8 @@ hb_status hb_set_tuning(hb_ctx* ctx, int mode, int TI, int TJ) {
   const bool pok = ctx->prec == HB_FP32 ? hbk::persist_available<float>(TI, TJ)
                                         : hbk::persist_available<double>(TI, TJ);
   if (mode == 1 && !pok) return fail(ctx, HB_ERR_UNSUPPORTED, "persistent driver not built for this shape");
+  if (mode == 1 && ctx->large_ns())
+    return fail(ctx, HB_ERR_UNSUPPORTED, "persistent driver: n_harm above HB_MAX_STATIC_HARMONICS");
   hb_status st = rebuild_tiles(ctx, TI, TJ, mode);
   if (st != HB_OK) return st;
   ctx->mode = mode;

@@ -8,7 +8,7 @@
 
 namespace hbk {
 
-constexpr int MAXNS = 9;       // 2 * HB_MAX_HARMONICS + 1
+constexpr int MAXNS = 31;      // 2 * HB_MAX_HARMONICS + 1
 constexpr int MAXNT = 256;     // threads per tile CTA
 
 // Per-case constants, in the kernel precision T.  Frames and freestream are
@@ -104,6 +104,7 @@ struct StageParams {
   double* partials;        // [ntiles][8] FP64 norm partials, or null
   T alpha;                 // RK stage coefficient
   int TI, TJ, ti_shift;    // tile shape; TI = 1 << ti_shift
+  const T* H;              // N_s > 9: HB source V omega D Uprev, same layout as the state
   const int2* job_range;   // RK mode: [ntiles] (first, count) into jobs, or null (no fused ghost fill)
   const GhostJob* jobs;
   const BcRec* job_bcs;
@@ -178,6 +179,12 @@ template <typename T>
 cudaError_t launch_forces(const ForceParams<T>& p, cudaStream_t s);
 template <typename T>
 cudaError_t launch_ghost_fill(const GhostFillParams<T>& p, cudaStream_t s);
+// H = V omega D U over the chunks (block, first padded cell) of 128 cells of
+// the blocks whose case has `ns` snapshots; D is that count's [ns][ns]
+// derivative matrix (host, FP64)
+template <typename T>
+cudaError_t launch_hb_source(const CaseDev<T>* cases, const BlockDev* blocks, Geo<T> g, const int2* chunks,
+                             int nchunks, int nv, int ns, const double* D, const T* U, T* H, cudaStream_t s);
 
 // SMs x resident CTAs of the RK-stage tile kernel (one wave of tiles)
 template <typename T>

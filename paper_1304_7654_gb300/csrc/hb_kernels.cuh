@@ -178,6 +178,12 @@ __device__ __forceinline__ void visc2d(const T* gL, const T* gR, T uL, T vL, T T
 // where the extra shared memory keeps the occupancy: up to 7 snapshots.
 __host__ __device__ constexpr bool tile_pipelined(int NS) { return NS <= 7; }
 
+// compile-time snapshot counts of the tile kernel; larger N_s run the
+// runtime-count instantiation (NS = 0)
+constexpr int kMaxStaticNS = 9;
+
+// (NS = 0: the runtime snapshot count of the large-N_s path, whose HB
+// source comes precomputed, so it keeps no per-snapshot balances)
 __host__ __device__ constexpr size_t tile2d_smem_elems(int TI, int TJ, int NS, bool pipe) {
   return (size_t)(pipe ? 15 : 10) * (TI + 4) * (TJ + 4) + (size_t)6 * (TI + 2) * (TJ + 2) +
          (size_t)4 * ((TI + 1) * TJ + TI * (TJ + 1)) + (size_t)NS * 4 * TI * TJ + (size_t)NS * NS;
@@ -350,7 +356,7 @@ __device__ __forceinline__ void fill_tile_ghosts(const StageParams<T>& P, int t,
   const int2 jr = P.job_range[t];
   if (jr.y <= 0) return;
   __syncthreads();   // own-cell outputs of every thread of the CTA are visible
-  const int nitem = jr.y * NS;
+  const int nitem = jr.y * (NS ? NS : C->ns);
   for (int w = threadIdx.x; w < nitem; w += blockDim.x) {
     const int n = w / jr.y;
     ghost_job<T>(C, P.g, P.blocks, P.job_bcs, P.jobs + jr.x + (w - n * jr.y), B, n, P.Unext, P.Unext);
@@ -371,7 +377,45 @@ __global__ void ghost_fill_kernel(GhostFillParams<T> p) {
   ghost_job<T>(C, p.g, p.blocks, p.bcs, J, R, n, p.src, p.dst);
 }
 
+// HB source of the large-N_s path, H = V omega D U (Sec. 2: the harmonic
+// balance operator couples every snapshot of a cell).  D depends on N_s
+// only; it travels as a kernel parameter, so every product takes its
+// coefficient from the constant bank while the cell's N_s values sit in
+// registers.  One thread per (padded cell, variable) of 128-cell chunks of
+// the blocks whose case has this N_s.
+constexpr int kSrcCells = 128;
+template <typename T, int NS>
+struct DMat {
+  T d[NS * NS];
+};
+
+template <typename T, int NS>
+__global__ void __launch_bounds__(kSrcCells) hb_source_kernel(const CaseDev<T>* cases, const BlockDev* blocks,
+                                                              Geo<T> g, const int2* chunks, int nv, DMat<T, NS> D,
+                                                              const T* U, T* H) {
+  const int2 ck = chunks[blockIdx.x];           // (block, first cell)
+  const int q = blockIdx.y;
+  const BlockDev& B = blocks[ck.x];
+  const int64_t c = (int64_t)ck.y + threadIdx.x;
+  if (c >= B.plane) return;
+  const T vw = g.q[G_VOL][B.goff + c] * cases[B.cs].omega;
+  const T* u = U + B.off + (int64_t)q * B.plane + c;
+  T x[NS];
+#pragma unroll
+  for (int m = 0; m < NS; ++m) x[m] = u[(int64_t)m * nv * B.plane];
+  T* h = H + B.off + (int64_t)q * B.plane + c;
+#pragma unroll
+  for (int n = 0; n < NS; ++n) {
+    T acc = T(0);
+#pragma unroll
+    for (int m = 0; m < NS; ++m) acc += D.d[n * NS + m] * x[m];
+    h[(int64_t)n * nv * B.plane] = vw * acc;
+  }
+}
+
 // MODE 0: R := residual.  MODE 1: RK stage update (+ norm partials if set).
+// NS = 0: the snapshot count is the case's (large N_s); the HB source comes
+// from P.H and each snapshot is updated as soon as its face fluxes are known.
 // The tile shape TI x TJ (TI a power of two) is a compile-time constant so that
 // every flat-index decomposition is a multiply-shift.
 template <typename T, int NS, bool VISC, int MODE, int TI, int TJ, bool PIPE>
@@ -405,6 +449,8 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   T* sF = sG + 6 * NG;     // [NV][NF] face fluxes
   T* sAcc = sF + 4 * NF;   // [NS][NV][NT] flux balance per snapshot of each own cell
   T* sD = sAcc + NS * NV * NT;   // [NS][NS]
+  constexpr bool DYN = NS == 0;
+  const int ns = DYN ? C->ns : NS;
 
   const T gam = C->gamma, gm1 = C->gamma - T(1), eps = C->eps, efrac = C->ent_frac;
   const T gg1 = gam / gm1, ig1 = T(1) / gm1;
@@ -555,15 +601,90 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
     for (int q = 0; q < 4; ++q) sF[q * NF + fq] = F[q];
   };
 
-  // flux balance of the own cell at snapshot n from the face fluxes
+  // ---- own-cell geometry that does not change with the snapshot (filled
+  // once the region's metrics are staged) and the RK update of one snapshot
+  T V = T(1), iV = T(1), a0x = T(0), a0y = T(0), b0x = T(0), b0y = T(0), ma2 = T(1), mb2 = T(1);
+  auto own_static = [&]() {
+    V = P.g.q[G_VOL][B.goff + cown];
+    iV = sIV[rown];
+    a0x = T(0.5) * (sS[rown] + sS[rown + 1]);
+    a0y = T(0.5) * (sS[NR + rown] + sS[NR + rown + 1]);
+    b0x = T(0.5) * (sS[2 * NR + rown] + sS[2 * NR + rown + RI]);
+    b0y = T(0.5) * (sS[3 * NR + rown] + sS[3 * NR + rown + RI]);
+    ma2 = a0x * a0x + a0y * a0y;
+    mb2 = b0x * b0x + b0y * b0y;
+  };
+  T tacc[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) tacc[q] = T(0);
+  // residual Rn of the own cell at snapshot n -> R, or the RK update of U0
+  // with the local time step (and the norm partial)
+  auto finish = [&](int n, const T* Rn) {
+    const int64_t base = B.off + (int64_t)n * NV * B.plane + cown;
+    if (MODE == 0) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) P.R[base + q * B.plane] = Rn[q];
+      return;
+    }
+    T u0[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) u0[q] = P.U0[base + q * B.plane];
+    const Fr<T> f = frame_at(C, n);
+    const T rho = u0[0], irho = Ar<T>::rcp(rho);
+    const T uv = u0[1] * irho, vv = u0[2] * irho;
+    const T pp = gm1 * (u0[3] - T(0.5) * rho * (uv * uv + vv * vv));
+    const T c2 = gam * pp * irho;
+    const T cs = c2 * Ar<T>::rsq(c2);
+    T urx = uv, ury = vv;
+    if (moving) {
+      T xc, yc;
+      rotp(f, P.g.q[G_XC][B.goff + cown], P.g.q[G_XC + 1][B.goff + cown], xc, yc);
+      urx -= -f.thd * (yc - f.py);
+      ury -= f.thd * (xc - f.px);
+    }
+    T ax, ay, bx, by;
+    rotv(f, a0x, a0y, ax, ay);
+    rotv(f, b0x, b0y, bx, by);
+    const T ma = ma2 * Ar<T>::rsq(ma2), mb = mb2 * Ar<T>::rsq(mb2);
+    T lam = fabs(urx * ax + ury * ay) + cs * ma + fabs(urx * bx + ury * by) + cs * mb;
+    if (VISC) {
+      const T cv = (gam / C->prandtl > T(4.0 / 3.0)) ? gam / C->prandtl : T(4.0 / 3.0);
+      lam += T(4) * cv * (mu * irho) * (ma2 + mb2) * iV;
+    }
+    lam += omega * T(C->nh) * V;
+    // dtau / V = cfl / lambda
+    const T fac = P.alpha * C->cfl * Ar<T>::rcp(lam);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) P.Unext[base + q * B.plane] = u0[q] - fac * Rn[q];
+    if (P.partials) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const T x = Rn[q] * iV;
+        tacc[q] += x * x;
+      }
+    }
+  };
+
+  // flux balance of the own cell at snapshot n from the face fluxes: kept
+  // for the epilogue, or (NS = 0) finished at once with the given HB source
   auto accumulate = [&](int n) {
     if (own) {
       const int fi0 = tj * (TI + 1) + ti;
       const int fj0 = NFI + tj * TI + ti;
+      T Rn[NV];
 #pragma unroll
       for (int q = 0; q < NV; ++q)
-        sAcc[(n * NV + q) * NT + tid] =
-            (sF[q * NF + fi0 + 1] - sF[q * NF + fi0]) + (sF[q * NF + fj0 + TI] - sF[q * NF + fj0]);
+        Rn[q] = (sF[q * NF + fi0 + 1] - sF[q * NF + fi0]) + (sF[q * NF + fj0 + TI] - sF[q * NF + fj0]);
+      if constexpr (DYN) {
+        if (n == 0) own_static();
+        const int64_t base = B.off + (int64_t)n * NV * B.plane + cown;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) Rn[q] += P.H[base + q * B.plane];
+        finish(n, Rn);
+      } else {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sAcc[(n * NV + q) * NT + tid] = Rn[q];
+      }
     }
   };
 
@@ -578,9 +699,9 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
       for (int gq = tid; gq < NGt; gq += nt) grad_cell(gq, f0, 0);
       __syncthreads();
     }
-    for (int n = 0; n < NS; ++n) {
+    for (int n = 0; n < ns; ++n) {
       const int b = n & 1;
-      const bool next = n + 1 < NS;
+      const bool next = n + 1 < ns;
       const Fr<T> f = frame_at(C, n);
       // one round-robin over faces then region cells: a thread with one face
       // fewer takes a region cell first
@@ -599,7 +720,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   } else {
     // per snapshot: staging, gradients, faces, balance; the staging of n+1
     // needs no barrier after the balance of n (which reads only the fluxes)
-    for (int n = 0; n < NS; ++n) {
+    for (int n = 0; n < ns; ++n) {
       const Fr<T> f = frame_at(C, n);
       for (int r = tid; r < NRt; r += nt) stage_cell(r, n, 0);
       __syncthreads();
@@ -614,78 +735,29 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
     __syncthreads();
   }
 
-  // ---- epilogue: HB source, residual or RK update, norm partials
-  T tacc[NV];
-#pragma unroll
-  for (int q = 0; q < NV; ++q) tacc[q] = T(0);
+  // ---- epilogue: HB source and residual or RK update (compile-time N_s)
   double nacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  if (own) {
-    const T V = P.g.q[G_VOL][B.goff + cown];
-    const T vw = V * omega;
-    const T iV = sIV[rown];
-    // the own cell at every snapshot (recently staged, served from cache)
-    T uu[NS][NV];
+  if constexpr (!DYN) {
+    if (own) {
+      own_static();
+      const T vw = V * omega;
+      // the own cell at every snapshot (recently staged, served from cache)
+      T uu[DYN ? 1 : NS][NV];
 #pragma unroll
-    for (int m = 0; m < NS; ++m)
+      for (int m = 0; m < NS; ++m)
 #pragma unroll
-      for (int q = 0; q < NV; ++q)
-        uu[m][q] = P.Uprev[B.off + ((int64_t)m * NV + q) * B.plane + cown];
-    // mean face vectors of the own cell (static frame)
-    const T a0x = T(0.5) * (sS[rown] + sS[rown + 1]), a0y = T(0.5) * (sS[NR + rown] + sS[NR + rown + 1]);
-    const T b0x = T(0.5) * (sS[2 * NR + rown] + sS[2 * NR + rown + RI]);
-    const T b0y = T(0.5) * (sS[3 * NR + rown] + sS[3 * NR + rown + RI]);
-    const T ma2 = a0x * a0x + a0y * a0y, mb2 = b0x * b0x + b0y * b0y;
-    const T ma = ma2 * Ar<T>::rsq(ma2), mb = mb2 * Ar<T>::rsq(mb2);
-    for (int n = 0; n < NS; ++n) {
-      T Rn[NV];
+        for (int q = 0; q < NV; ++q)
+          uu[m][q] = P.Uprev[B.off + ((int64_t)m * NV + q) * B.plane + cown];
+      for (int n = 0; n < NS; ++n) {
+        T Rn[NV];
 #pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        T h = T(0);
+        for (int q = 0; q < NV; ++q) {
+          T h = T(0);
 #pragma unroll
-        for (int m = 0; m < NS; ++m) h += sD[n * NS + m] * uu[m][q];
-        Rn[q] = sAcc[(n * NV + q) * NT + tid] + vw * h;
-      }
-      const int64_t base = B.off + (int64_t)n * NV * B.plane + cown;
-      if (MODE == 0) {
-#pragma unroll
-        for (int q = 0; q < NV; ++q) P.R[base + q * B.plane] = Rn[q];
-      } else {
-        T u0[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) u0[q] = P.U0[base + q * B.plane];
-        const Fr<T> f = frame_at(C, n);
-        const T rho = u0[0], irho = Ar<T>::rcp(rho);
-        const T uv = u0[1] * irho, vv = u0[2] * irho;
-        const T pp = gm1 * (u0[3] - T(0.5) * rho * (uv * uv + vv * vv));
-        const T c2 = gam * pp * irho;
-        const T cs = c2 * Ar<T>::rsq(c2);
-        T urx = uv, ury = vv;
-        if (moving) {
-          T xc, yc;
-          rotp(f, P.g.q[G_XC][B.goff + cown], P.g.q[G_XC + 1][B.goff + cown], xc, yc);
-          urx -= -f.thd * (yc - f.py);
-          ury -= f.thd * (xc - f.px);
+          for (int m = 0; m < NS; ++m) h += sD[n * NS + m] * uu[m][q];
+          Rn[q] = sAcc[(n * NV + q) * NT + tid] + vw * h;
         }
-        T ax, ay, bx, by;
-        rotv(f, a0x, a0y, ax, ay);
-        rotv(f, b0x, b0y, bx, by);
-        T lam = fabs(urx * ax + ury * ay) + cs * ma + fabs(urx * bx + ury * by) + cs * mb;
-        if (VISC) {
-          const T cv = (gam / C->prandtl > T(4.0 / 3.0)) ? gam / C->prandtl : T(4.0 / 3.0);
-          lam += T(4) * cv * (mu * irho) * (ma2 + mb2) * iV;
-        }
-        lam += omega * T(C->nh) * V;
-        // dtau / V = cfl / lambda
-        const T fac = P.alpha * C->cfl * Ar<T>::rcp(lam);
-#pragma unroll
-        for (int q = 0; q < NV; ++q) P.Unext[base + q * B.plane] = u0[q] - fac * Rn[q];
-        if (P.partials) {
-#pragma unroll
-          for (int q = 0; q < NV; ++q) {
-            const T x = Rn[q] * iV;
-            tacc[q] += x * x;
-          }
-        }
+        finish(n, Rn);
       }
     }
   }

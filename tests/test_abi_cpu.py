@@ -33,8 +33,10 @@ def _create(case, prec=hb.HB_FP64):
 
 
 def test_rejects_harmonics_above_maximum(lib):
-    cs = C.channel(8, 4, n_harm=5)
+    # 2D up to N_H = 15 (the paper's 31 snapshots); 3D up to N_H = 4
+    cs = C.channel(8, 4, n_harm=16)
     assert _create(cs) == hb.HB_ERR_UNSUPPORTED
+    assert _create(C.box3d(4, 4, 4, n_harm=5)) == hb.HB_ERR_UNSUPPORTED
 
 
 def test_rejects_cut_outside_ghost_layers(lib):
