@@ -261,6 +261,22 @@ hb_status hb_kernel_stats(hb_ctx* ctx, int which, double* ms, int64_t* launches,
 hb_status hb_residual_norms_noalloc(const void* R, const void* vol, int prec, int64_t ncells,
                                     int n_snap, int nv, double* norms, void* stream);
 
+/* Restart files (the paper's restart file, Sec. 3.2): hb_save_state writes the
+ * interior cells of the device state U, in the context's precision and in the
+ * compact order [block][snapshot][variable][k][j][i], after a header with a
+ * format version, the iteration number given by the caller and a signature
+ * of the context (dimension, precision, cases, block sizes, snapshot counts
+ * and flow parameters).  hb_load_state checks the signature and writes the
+ * interior cells of U (ghost cells are not stored: every RK call fills
+ * them), returning the stored iteration.  A run of n iterations, saved,
+ * loaded and continued for m more, equals a run of n + m iterations bit for
+ * bit.  Both synchronise `stream` (host file I/O).  Errors:
+ * HB_ERR_INVALID_ARG for null arguments, an unreadable or unwritable file, a
+ * truncated file, another format or a signature of another context;
+ * HB_ERR_CUDA if a copy fails. */
+hb_status hb_save_state(hb_ctx* ctx, const void* U, const char* path, int64_t iteration, void* stream);
+hb_status hb_load_state(hb_ctx* ctx, void* U, const char* path, int64_t* iteration, void* stream);
+
 /* Synchronise `stream`, then read and clear the device error word. */
 hb_status hb_sync_status(hb_ctx* ctx, void* stream);
 

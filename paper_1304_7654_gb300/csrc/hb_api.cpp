@@ -1506,6 +1506,106 @@ hb_status init_impl(hb_ctx* c, T* U, const double* noise, double amp, cudaStream
 }  // namespace
 
 // ================================================================== C ABI
+// ---- restart files
+namespace {
+constexpr char kCkptMagic[8] = {'H', 'B', 'R', 'E', 'S', 'T', 'R', '1'};
+
+// FNV-1a over the context's defining integers and flow parameters
+uint64_t ctx_signature(const hb_ctx* c) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t k = 0; k < n; ++k) { h ^= b[k]; h *= 1099511628211ull; }
+  };
+  mix(&c->dim, sizeof(int));
+  mix(&c->prec, sizeof(int));
+  const int nc = (int)c->cases.size();
+  mix(&nc, sizeof(int));
+  for (const CaseHost& ch : c->cases) {
+    const hb_case_desc& d = ch.d;
+    mix(&d.n_harm, sizeof(int));
+    mix(&d.n_blocks, sizeof(int));
+    mix(&d.viscous, sizeof(int));
+    const double prm[6] = {d.mach, d.reynolds, d.gamma, d.omega, d.alpha0_deg, d.pitch_amp_deg};
+    mix(prm, sizeof(prm));
+  }
+  for (const BlockDev& B : c->blocks) mix(B.n, sizeof(B.n));
+  return h;
+}
+
+struct CkptHeader {
+  char magic[8];
+  uint64_t signature;
+  int64_t values;       // interior values stored
+  int64_t iteration;
+  int32_t prec, pad;
+};
+
+// host copy of the interior of every block in compact order, or the reverse
+template <typename T>
+void interior_copy(const hb_ctx* c, std::vector<T>& full, std::vector<T>& compact, bool to_compact) {
+  int64_t q = 0;
+  for (const CaseHost& ch : c->cases)
+    for (int b = ch.block0; b < ch.block0 + ch.nblocks; ++b) {
+      const BlockDev& B = c->blocks[b];
+      for (int n = 0; n < ch.ns; ++n)
+        for (int v = 0; v < c->nv; ++v)
+          for (int k = 0; k < B.n[2]; ++k)
+            for (int j = 0; j < B.n[1]; ++j)
+              for (int i = 0; i < B.n[0]; ++i, ++q) {
+                const int64_t e = B.off + ((int64_t)n * c->nv + v) * B.plane + pcell(B, i, j, k);
+                if (to_compact) compact[q] = full[e];
+                else full[e] = compact[q];
+              }
+    }
+}
+
+template <typename T>
+hb_status save_impl(hb_ctx* c, const T* U, const char* path, int64_t it, cudaStream_t s) {
+  std::vector<T> full((size_t)c->state_size), comp((size_t)c->interior_values);
+  HB_CUDA(c, cudaMemcpyAsync(full.data(), U, sizeof(T) * full.size(), cudaMemcpyDeviceToHost, s));
+  HB_CUDA(c, cudaStreamSynchronize(s));
+  interior_copy<T>(c, full, comp, true);
+  CkptHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, kCkptMagic, 8);
+  h.signature = ctx_signature(c);
+  h.values = c->interior_values;
+  h.iteration = it;
+  h.prec = c->prec;
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(c, HB_ERR_INVALID_ARG, std::string("cannot write ") + path);
+  const bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(comp.data(), sizeof(T), comp.size(), f) == comp.size();
+  if (fclose(f) != 0 || !ok) return fail(c, HB_ERR_INVALID_ARG, std::string("write failed: ") + path);
+  return HB_OK;
+}
+
+template <typename T>
+hb_status load_impl(hb_ctx* c, T* U, const char* path, int64_t* it, cudaStream_t s) {
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(c, HB_ERR_INVALID_ARG, std::string("cannot read ") + path);
+  CkptHeader h;
+  std::vector<T> comp((size_t)c->interior_values);
+  bool ok = fread(&h, sizeof(h), 1, f) == 1;
+  if (ok && (memcmp(h.magic, kCkptMagic, 8) != 0 || h.prec != c->prec || h.values != c->interior_values ||
+             h.signature != ctx_signature(c))) {
+    fclose(f);
+    return fail(c, HB_ERR_INVALID_ARG, std::string("restart file of another format or context: ") + path);
+  }
+  ok = ok && fread(comp.data(), sizeof(T), comp.size(), f) == comp.size();
+  fclose(f);
+  if (!ok) return fail(c, HB_ERR_INVALID_ARG, std::string("truncated restart file: ") + path);
+  std::vector<T> full((size_t)c->state_size);
+  HB_CUDA(c, cudaMemcpyAsync(full.data(), U, sizeof(T) * full.size(), cudaMemcpyDeviceToHost, s));
+  HB_CUDA(c, cudaStreamSynchronize(s));
+  interior_copy<T>(c, full, comp, false);
+  HB_CUDA(c, cudaMemcpyAsync(U, full.data(), sizeof(T) * full.size(), cudaMemcpyHostToDevice, s));
+  HB_CUDA(c, cudaStreamSynchronize(s));
+  if (it) *it = h.iteration;
+  return HB_OK;
+}
+}  // namespace
+
 extern "C" {
 
 hb_status hb_create(const hb_case_desc* desc, hb_ctx** out) { return create_impl(desc, 1, out); }
@@ -1682,6 +1782,20 @@ hb_status hb_kernel_stats(hb_ctx* ctx, int which, double* ms, int64_t* launches,
     ctx->n_launch = 0;
   }
   return HB_OK;
+}
+
+hb_status hb_save_state(hb_ctx* ctx, const void* U, const char* path, int64_t iteration, void* stream) {
+  if (!ctx || !U || !path) return fail(ctx, HB_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  return ctx->prec == HB_FP32 ? save_impl<float>(ctx, (const float*)U, path, iteration, s)
+                              : save_impl<double>(ctx, (const double*)U, path, iteration, s);
+}
+
+hb_status hb_load_state(hb_ctx* ctx, void* U, const char* path, int64_t* iteration, void* stream) {
+  if (!ctx || !U || !path) return fail(ctx, HB_ERR_INVALID_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  return ctx->prec == HB_FP32 ? load_impl<float>(ctx, (float*)U, path, iteration, s)
+                              : load_impl<double>(ctx, (double*)U, path, iteration, s);
 }
 
 hb_status hb_sync_status(hb_ctx* ctx, void* stream) {

@@ -103,6 +103,8 @@ def load(path: str | None = None):
                                     ct.c_int]
     lib.hb_residual_norms_noalloc.argtypes = [_vp, _vp, ct.c_int, ct.c_int64, ct.c_int, ct.c_int,
                                               _vp, _vp]
+    lib.hb_save_state.argtypes = [_vp, _vp, ct.c_char_p, ct.c_int64, _vp]
+    lib.hb_load_state.argtypes = [_vp, _vp, ct.c_char_p, ct.POINTER(ct.c_int64), _vp]
     lib.hb_last_error.restype = ct.c_char_p
     lib.hb_last_error.argtypes = [_vp]
     _lib = lib
@@ -323,6 +325,16 @@ class HBContext:
         ms, n = ct.c_double(), ct.c_int64()
         self._check(self.lib.hb_kernel_stats(self.h, int(which), ct.byref(ms), ct.byref(n), int(reset)))
         return float(ms.value), int(n.value)
+
+    def save_state(self, U, path, iteration=0):
+        """hb_save_state: restart file of U's interior cells with `iteration`."""
+        self._check(self.lib.hb_save_state(self.h, _ptr(U), os.fsencode(path), int(iteration), _stream()))
+
+    def load_state(self, U, path):
+        """hb_load_state into U; returns the stored iteration."""
+        it = ct.c_int64(0)
+        self._check(self.lib.hb_load_state(self.h, _ptr(U), os.fsencode(path), ct.byref(it), _stream()))
+        return int(it.value)
 
     def sync_status(self):
         return int(self.lib.hb_sync_status(self.h, _stream()))
