@@ -261,7 +261,7 @@ hb_status hb_kernel_stats(hb_ctx* ctx, int which, double* ms, int64_t* launches,
 hb_status hb_residual_norms_noalloc(const void* R, const void* vol, int prec, int64_t ncells,
                                     int n_snap, int nv, double* norms, void* stream);
 
-/* Restart files (the paper's restart file, Sec. 3.2): hb_save_state writes the
+/* Restart files (the paper's restart file, Sec. 3.1): hb_save_state writes the
  * interior cells of the device state U, in the context's precision and in the
  * compact order [block][snapshot][variable][k][j][i], after a header with a
  * format version, the iteration number given by the caller and a signature

@@ -377,8 +377,8 @@ __global__ void ghost_fill_kernel(GhostFillParams<T> p) {
   ghost_job<T>(C, p.g, p.blocks, p.bcs, J, R, n, p.src, p.dst);
 }
 
-// HB source of the large-N_s path, H = V omega D U (Sec. 2: the harmonic
-// balance operator couples every snapshot of a cell).  D depends on N_s
+// HB source of the large-N_s path, H = V omega D U (the harmonic balance
+// operator of the HB solver, Sec. 1, couples every snapshot of a cell).  D depends on N_s
 // only; it travels as a kernel parameter, so every product takes its
 // coefficient from the constant bank while the cell's N_s values sit in
 // registers.  One thread per (padded cell, variable) of 128-cell chunks of

@@ -2,11 +2,11 @@
 whose value derives from its own cells (cut copies and chains of boundary
 maps resolved on the host), so no halo pass runs between stages.
 
-Checked against the explicit pass-ordered halo exchange (the same boundary
-maps applied pass by pass, Sec. 3.1's multi-block halo with the boundary
-conditions of Sec. 2): the ghosts the stages leave behind equal a fresh
-exchange of the result, and the drivers with and without the fusion give the
-same state."""
+Checked against hb_exchange_halos (the multi-block halo of Sec. 3.1 with
+the boundary conditions read for the solver; the parity tests pin it to the
+oracle's pass-ordered fill on every padded cell): the ghosts the stages leave
+behind equal a fresh exchange of the result, and the drivers with and
+without the fusion give the same state."""
 import numpy as np
 import pytest
 import torch

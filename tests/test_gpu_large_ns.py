@@ -1,6 +1,6 @@
 """Large snapshot counts (N_s = 17 and 31, the paper's two test cases,
 Sec. 4.1): the tile kernel runs with the case's snapshot count at run time
-and takes the HB source V omega D U (Sec. 2) from a separate launch.
+and takes the HB source V omega D U (Sec. 1) from a separate launch.
 Parity with the FP64 oracle on the residual and on RK trajectories, a batch
 mixing small and large N_s, and the drivers that refuse large N_s."""
 import numpy as np

@@ -1,5 +1,5 @@
 """Restart files (hb_save_state / hb_load_state, the paper's restart file of
-Sec. 3.2): a run saved after n iterations and resumed in a fresh context
+Sec. 3.1): a run saved after n iterations and resumed in a fresh context
 equals the uninterrupted run bit for bit; files of another context,
 precision or format, and truncated files, are refused."""
 import os
