@@ -104,6 +104,11 @@ struct Case {
   int64_t total;
   std::vector<double> D;  // ns x ns
   double mu, kappa, pinf;
+  // time-domain mode (one snapshot at physical time td_t): the frame, grid
+  // velocity and unsteady inflow are those of td_t instead of t_0 = 0
+  int td = 0;
+  double td_t = 0.0;
+  double td_lam = 0.0;    // a0 / dt: the physical-time term's share of the pseudo-time step
   int64_t at(int b, int n, int v, int64_t c) const {
     return boff[b] + ((int64_t)n * nv + v) * B[b].ncell + c;
   }
@@ -205,6 +210,7 @@ struct Frame { double c, s, thdot, t, px, py; };
 Frame frame(const Case& C, int n) {
   Frame f;
   f.t = (C.omega > 0.0) ? 2.0 * M_PI * n / (C.ns * C.omega) : 0.0;
+  if (C.td) f.t = C.td_t;
   double th = 0.0, thd = 0.0;
   if (C.motion == 1) {
     th = C.pitch_amp * std::sin(C.omega * f.t);
@@ -683,6 +689,7 @@ double local_dt(const Case& C, const double* U0, int b, int i, int j, int k, int
   double V = B.vol[c];
   if (C.viscous) lam += 4.0 * std::max(4.0 / 3.0, C.gamma / C.prandtl) * (C.mu / W[0]) * s2 / V;
   lam += C.omega * C.nh * V;
+  lam += C.td_lam * V;
   return C.cfl * V / lam;
 }
 
@@ -916,6 +923,98 @@ void orc_rk_smooth(void* h, double* U, int n_iter, double* norms) {
           norms[(int64_t)it * C->nv + v] = std::sqrt(acc[v] / (double)(ncells * C->ns));
     }
   }
+}
+
+// ---- time-domain dual time stepping (a case with one snapshot).  Reading:
+// the physical-time derivative by second-order backward differences (BDF2),
+// each physical step solved by the same pseudo-time RK smoother with local
+// time steps:  R*(U) = R(U; t) + V (a0 U + a1 U^n + a2 U^(n-1)) / dt,
+// (a0, a1, a2) = (3/2, -2, 1/2), or (1, -1, 0) on the first step (U^(n-1)
+// null); the pseudo time step adds a0 V / dt to its spectral radius.
+namespace {
+void td_coeffs(const double* Unm1, double* a) {
+  if (Unm1) { a[0] = 1.5; a[1] = -2.0; a[2] = 0.5; }
+  else { a[0] = 1.0; a[1] = -1.0; a[2] = 0.0; }
+}
+
+void td_residual(Case& C, const double* U, const double* Un, const double* Unm1, double dt, double* R) {
+  double a[3];
+  td_coeffs(Unm1, a);
+  std::vector<double> W(U, U + C.total), r(C.nv);
+  fill_ghosts(C, W.data());
+  std::fill(R, R + C.total, 0.0);
+  for_interior(C, [&](int b, int i, int j, int k) {
+    cell_residual(C, (const double*)W.data(), b, i, j, k, r.data(), (double*)nullptr);
+    const int64_t c = C.B[b].cell(i, j, k);
+    const double V = C.B[b].vol[c];
+    for (int v = 0; v < C.nv; ++v) {
+      const int64_t e = C.at(b, 0, v, c);
+      const double ut = a[0] * U[e] + a[1] * Un[e] + (Unm1 ? a[2] * Unm1[e] : 0.0);
+      R[e] = r[v] + V * ut / dt;
+    }
+  });
+}
+}  // namespace
+
+// R*(U) at physical time t (interior entries; the case has one snapshot)
+void orc_td_residual(void* h, const double* U, const double* Un, const double* Unm1, double t, double dt,
+                     double* R) {
+  Case* C = (Case*)h;
+  C->td = 1;
+  C->td_t = t;
+  td_residual(*C, U, Un, Unm1, dt, R);
+  C->td = 0;
+}
+
+// n_inner pseudo-time RK iterations of R*(U) = 0 at physical time t, in
+// place; norms[it][v] = RMS of R*/V at the first stage, or NULL
+void orc_td_step(void* h, double* U, const double* Un, const double* Unm1, double t, double dt, int n_inner,
+                 double* norms) {
+  Case* C = (Case*)h;
+  double a[3];
+  td_coeffs(Unm1, a);
+  C->td = 1;
+  C->td_t = t;
+  C->td_lam = a[0] / dt;
+  const double alpha[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
+  std::vector<double> U0(C->total), dtl(C->total), R(C->total);
+  int64_t ncells = 0;
+  for (auto& B : C->B) ncells += (int64_t)B.n[0] * B.n[1] * B.n[2];
+  for (int it = 0; it < n_inner; ++it) {
+    std::copy(U, U + C->total, U0.begin());
+    for_interior(*C, [&](int b, int i, int j, int k) {
+      dtl[C->at(b, 0, 0, C->B[b].cell(i, j, k))] = local_dt(*C, U0.data(), b, i, j, k, 0);
+    });
+    for (int s = 0; s < 4; ++s) {
+      td_residual(*C, U, Un, Unm1, dt, R.data());
+      double acc[5] = {0, 0, 0, 0, 0};
+      for_interior(*C, [&](int b, int i, int j, int k) {
+        const int64_t c = C->B[b].cell(i, j, k);
+        const double V = C->B[b].vol[c];
+        const double tl = dtl[C->at(b, 0, 0, c)];
+        for (int v = 0; v < C->nv; ++v) {
+          const int64_t e = C->at(b, 0, v, c);
+          if (s == 0) acc[v] += (R[e] / V) * (R[e] / V);
+          U[e] = U0[e] - alpha[s] * tl / V * R[e];
+        }
+      });
+      if (s == 0 && norms)
+        for (int v = 0; v < C->nv; ++v) norms[(int64_t)it * C->nv + v] = std::sqrt(acc[v] / (double)ncells);
+    }
+  }
+  C->td = 0;
+  C->td_lam = 0.0;
+}
+
+// forces at physical time t of a one-snapshot case
+void orc_td_forces(void* h, const double* Uin, double t, double* coef, double* J) {
+  Case* C = (Case*)h;
+  C->td = 1;
+  C->td_t = t;
+  std::vector<double> U(Uin, Uin + C->total);
+  fill_ghosts(*C, U.data());
+  forces(*C, U.data(), coef, J);
+  C->td = 0;
 }
 
 void orc_forces(void* h, const double* Uin, double* coef, double* J) {

@@ -58,6 +58,9 @@ def _load():
             lib.orc_time_step.argtypes = [ct.c_void_p, _dp, _dp]
             lib.orc_rk_smooth.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp]
             lib.orc_forces.argtypes = [ct.c_void_p, _dp, _dp, _dp]
+            lib.orc_td_residual.argtypes = [ct.c_void_p, _dp, _dp, _dp, ct.c_double, ct.c_double, _dp]
+            lib.orc_td_step.argtypes = [ct.c_void_p, _dp, _dp, _dp, ct.c_double, ct.c_double, ct.c_int, _dp]
+            lib.orc_td_forces.argtypes = [ct.c_void_p, _dp, ct.c_double, _dp, _dp]
             lib.orc_adjoint_columns.argtypes = [ct.c_void_p, _dp, _dp, ct.c_double, ct.c_int, _ip,
                                                 _dp, ct.c_int, ct.c_double]
             lib.orc_d_matrix.argtypes = [ct.c_int, _dp]
@@ -227,6 +230,34 @@ class Oracle:
         coef = np.zeros((self.ns, nb, 3))
         J = ct.c_double()
         self.lib.orc_forces(self.h, _d(U), _d(coef), ct.byref(J))
+        return coef[:, :self.case.n_bodies], float(J.value)
+
+    # ---- time-domain dual time stepping (cases with n_harm = 0)
+    def td_residual(self, U, Un, Unm1, t, dt):
+        """R*(U) = R(U; t) + V (a0 U + a1 U^n + a2 U^(n-1)) / dt (BDF2, or BDF1
+        when Unm1 is None), interior entries."""
+        assert self.ns == 1, "time-domain stepping needs a one-snapshot case"
+        U, Un = _f64(U), _f64(Un)
+        R = np.zeros(self.size)
+        self.lib.orc_td_residual(self.h, _d(U), _d(Un), None if Unm1 is None else _d(_f64(Unm1)),
+                                 float(t), float(dt), _d(R))
+        return R
+
+    def td_step(self, U, Un, Unm1, t, dt, n_inner):
+        """n_inner pseudo-time RK iterations of R*(U) = 0 at time t."""
+        assert self.ns == 1, "time-domain stepping needs a one-snapshot case"
+        U = _f64(U).copy()
+        norms = np.zeros((max(n_inner, 1), self.nv))
+        self.lib.orc_td_step(self.h, _d(U), _d(_f64(Un)), None if Unm1 is None else _d(_f64(Unm1)),
+                             float(t), float(dt), int(n_inner), _d(norms))
+        return U, norms[:n_inner]
+
+    def td_forces(self, U, t):
+        U = _f64(U)
+        nb = max(self.case.n_bodies, 1)
+        coef = np.zeros((1, nb, 3))
+        J = ct.c_double()
+        self.lib.orc_td_forces(self.h, _d(U), float(t), _d(coef), ct.byref(J))
         return coef[:, :self.case.n_bodies], float(J.value)
 
     def adjoint_columns(self, U, psi, J_seed, cols, mode=0, h=1e-7) -> np.ndarray:

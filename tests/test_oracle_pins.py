@@ -517,3 +517,51 @@ def test_multiblock_equals_single_block_3d():
     ref = split(o1.unpack(R1).reshape(shp))
     sc = split(o1.unpack(S1).reshape(shp))
     assert np.max(np.abs(om.unpack(Rm) - ref) / sc) < 1e-14
+
+
+# ------------------------------------------- time-domain dual time stepping --
+def test_td_bdf2_term_is_exact_for_quadratics_in_time():
+    # on a doubly periodic grid a spatially uniform state has zero flux
+    # balance (closed cells), so R* / V is the time term alone; BDF2 is exact
+    # for states quadratic in t: R*/V = dU/dt = B + 2 C t at t_(k+1)
+    cs = C.periodic_box2d(8, 6, n_harm=0)
+    o = Oracle(cs)
+    A = np.array([1.0, 0.3, -0.1, 0.8])
+    B = np.array([0.02, -0.01, 0.03, 0.05])
+    Cq = np.array([0.004, 0.002, -0.003, 0.001])
+    t1, dt = 0.7, 0.05
+    at = lambda t: A + B * t + Cq * t * t
+
+    def state(t):   # conservative variables uniform in space
+        flat = np.concatenate([np.repeat(at(t)[:, None], b.n[0] * b.n[1], axis=1).ravel() for b in cs.blocks])
+        return o.pack(flat)
+
+    vols = [o.geometry(b)[0][0, 2:-2, 2:-2].ravel() for b in range(len(cs.blocks))]
+
+    def per_var(R):
+        out, k = [], 0
+        for b, blk in enumerate(cs.blocks):
+            m = blk.n[0] * blk.n[1]
+            for v in range(4):
+                out.append((v, R[k:k + m] / vols[b]))
+                k += m
+        return out
+
+    U, Un, Unm1 = state(t1), state(t1 - dt), state(t1 - 2 * dt)
+    for v, got in per_var(o.unpack(o.td_residual(U, Un, Unm1, t1, dt))):
+        assert np.allclose(got, B[v] + 2 * Cq[v] * t1, rtol=0, atol=1e-11), v
+    # the first step (no U^(n-1)) is backward Euler: (U - U^n) / dt
+    for v, got in per_var(o.unpack(o.td_residual(U, Un, None, t1, dt))):
+        assert np.allclose(got, (at(t1)[v] - at(t1 - dt)[v]) / dt, rtol=0, atol=1e-11), v
+
+
+def test_td_residual_at_rest_in_time_is_the_steady_residual():
+    # U = U^n = U^(n-1): the time term vanishes; at t = 0 the frame is the one
+    # of the single HB snapshot, so R* equals the N_H = 0 residual
+    cs = C.ogrid(24, 8, n_harm=0, viscous=True, pitch_deg=3.0)
+    o = Oracle(cs)
+    U = o.init_state(C.noise(cs), 0.01)
+    R0 = o.residual(U, with_scale=False)
+    Rt = o.td_residual(U, U, U, 0.0, 0.1)
+    # (3/2 - 2 + 1/2) U is zero up to the rounding of the BDF combination
+    assert np.abs(o.unpack(Rt) - o.unpack(R0)).max() <= 1e-12 * np.abs(o.unpack(R0)).max()
