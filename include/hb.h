@@ -277,6 +277,27 @@ hb_status hb_residual_norms_noalloc(const void* R, const void* vol, int prec, in
 hb_status hb_save_state(hb_ctx* ctx, const void* U, const char* path, int64_t iteration, void* stream);
 hb_status hb_load_state(hb_ctx* ctx, void* U, const char* path, int64_t* iteration, void* stream);
 
+/* Time-domain dual time stepping on the same kernels (contexts whose cases
+ * all have n_harm = 0, 2D): one physical time step to time t of size dt,
+ * i.e. n_inner pseudo-time RK iterations (4 stages, local time steps) in
+ * place on U (device, state layout; start it from U_n) of
+ *     R*(U) = R(U; t) + V (a0 U + a1 U_n + a2 U_nm1) / dt = 0,
+ * (a0, a1, a2) = (3/2, -2, 1/2) (second-order backward differences), or
+ * (1, -1, 0) when U_nm1 is NULL (first step); the pseudo time step adds
+ * a0 V / dt to the spectral radius.  R(U; t) is the residual with the grid
+ * pitched, moving and the inflow as at time t; the context keeps that frame
+ * afterwards (hb_forces and hb_residual then refer to t).  norms (device,
+ * may be NULL): [n_inner][n_cases][nv] FP64 RMS of R* / V at the first stage.
+ * The HB residual's time-derivative source V omega D U is the periodic
+ * counterpart of this term: a converged HB solution equals the periodic
+ * limit of these steps up to the harmonics above N_H (Sec. 1: the HB solver
+ * replaces the time-domain one for periodic flows).  Errors:
+ * HB_ERR_INVALID_ARG (null U or U_n, dt <= 0, t < 0, n_inner < 0),
+ * HB_ERR_UNSUPPORTED (3D, or a case with n_harm > 0).  Asynchronous on
+ * `stream` after a short host synchronisation for the frame upload. */
+hb_status hb_td_step(hb_ctx* ctx, void* U, const void* U_n, const void* U_nm1, double t, double dt,
+                     int n_inner, double* norms, void* stream);
+
 /* Synchronise `stream`, then read and clear the device error word. */
 hb_status hb_sync_status(hb_ctx* ctx, void* stream);
 

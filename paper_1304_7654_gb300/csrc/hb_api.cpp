@@ -94,6 +94,10 @@ struct hb_ctx {
   std::vector<SrcGroup> src_groups;
   void* d_H = nullptr;
   bool large_ns() const { return nchunks > 0; }
+  // time-domain stepping: chunks over every block (built on first use)
+  int2* d_td_chunks = nullptr;
+  int n_td_chunks = 0;
+  std::vector<unsigned char> td_case_buf;
   int n_bodies = 0;
   void* d_A = nullptr;          // RK ping-pong and residual scratch
   void* d_B = nullptr;
@@ -478,8 +482,10 @@ hb_status resolve_ghost_jobs(hb_ctx* ctx, const Tables& T, const int* bc_index) 
   return HB_OK;
 }
 
+// per-case constants; td_time >= 0: one snapshot at that physical time
+// (time-domain stepping) instead of the HB snapshot times
 template <typename T>
-void fill_case_dev(const CaseHost& ch, CaseDev<T>& C) {
+void fill_case_dev(const CaseHost& ch, CaseDev<T>& C, double td_time = -1.0) {
   const hb_case_desc& d = ch.d;
   memset(&C, 0, sizeof(C));
   C.dim = d.dim;
@@ -526,7 +532,7 @@ void fill_case_dev(const CaseHost& ch, CaseDev<T>& C) {
     }
   const double amp = d.pitch_amp_deg * M_PI / 180.0;
   for (int n = 0; n < ns; ++n) {
-    const double t = (d.omega > 0.0) ? 2.0 * M_PI * n / (ns * d.omega) : 0.0;
+    const double t = (td_time >= 0.0) ? td_time : (d.omega > 0.0) ? 2.0 * M_PI * n / (ns * d.omega) : 0.0;
     double th = 0.0, thd = 0.0;
     if (d.motion == HB_MOTION_PITCH) {
       th = amp * std::sin(d.omega * t);
@@ -572,6 +578,7 @@ void free_ctx(hb_ctx* c) {
   cudaFree(c->d_job_bcs);
   cudaFree(c->d_chunks);
   cudaFree(c->d_H);
+  cudaFree(c->d_td_chunks);
   cudaFree(c->d_A);
   cudaFree(c->d_B);
   cudaFree(c->d_partials);
@@ -1187,11 +1194,16 @@ hb_status stage_all(hb_ctx* c, hbk::StageParams<T> p, int mode, cudaStream_t s) 
     if (part) p.partials = part + (size_t)8 * ch.tile0;
     const int2* jr = p.job_range;
     if (jr) p.job_range = jr + ch.tile0;
+    // the precomputed source serves the large-N_s cases (and time-domain
+    // steps); the other cases of a batch form their HB source in the tile
+    const T* H = p.H;
+    if (p.lam_v == T(0) && ch.ns <= 2 * HB_MAX_STATIC_HARMONICS + 1) p.H = nullptr;
     TimedScope ts(c, 0, s);
     if (c->dim == 3) HB_CUDA(c, hbk::launch_stage3d<T>(p, ch.ns, c->viscous, mode, s));
     else HB_CUDA(c, hbk::launch_stage<T>(p, ch.ns, c->viscous, mode, s));
     p.partials = part;
     p.job_range = jr;
+    p.H = H;
   }
   return HB_OK;
 }
@@ -1220,7 +1232,7 @@ hb_status residual_impl(hb_ctx* c, const T* U, T* R, cudaStream_t s) {
   p.R = R;
   st = hb_source<T>(c, W, s);
   if (st != HB_OK) return st;
-  p.H = (const T*)c->d_H;
+  if (c->large_ns()) p.H = (const T*)c->d_H;
   return stage_all<T>(c, p, 0, s);
 }
 
@@ -1249,7 +1261,7 @@ hb_status rk_iteration(hb_ctx* c, T* U, double* norm_out, cudaStream_t s) {
     p.partials = (st == 0) ? c->d_partials : nullptr;
     r = hb_source<T>(c, in[st], s);
     if (r != HB_OK) return r;
-    p.H = (const T*)c->d_H;
+    if (c->large_ns()) p.H = (const T*)c->d_H;
     r = stage_all<T>(c, p, 1, s);
     if (r != HB_OK) return r;
     if (st == 0) {
@@ -1333,6 +1345,84 @@ hb_status copy_norms(hb_ctx* c, double* norms, int done, int K, cudaStream_t s) 
   HB_CUDA(c, cudaMemcpy2DAsync(norms + (size_t)done * nc * c->nv, sizeof(double) * c->nv, c->d_ring,
                                sizeof(double) * 8, sizeof(double) * c->nv, (size_t)K * nc,
                                cudaMemcpyDeviceToDevice, s));
+  return HB_OK;
+}
+
+// ---- time-domain dual time stepping: one-snapshot cases at physical time t
+template <typename T>
+hb_status td_iteration(hb_ctx* c, T* U, const T* Un, const T* Unm1, double dt, double* norm_out,
+                       cudaStream_t s) {
+  static const double alpha[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
+  // BDF2, or backward Euler on the first step
+  const double a0 = Unm1 ? 1.5 : 1.0, a1 = Unm1 ? -2.0 : -1.0, a2 = Unm1 ? 0.5 : 0.0;
+  T* A = (T*)c->d_A;
+  T* Bf = (T*)c->d_B;
+  T* in[4] = {U, A, Bf, A};
+  T* out[4] = {A, Bf, A, U};
+  for (int st = 0; st < 4; ++st) {
+    {
+      TimedScope ts(c, 1, s);
+      HB_CUDA(c, hbk::launch_td_source<T>(c->d_blocks, geo_of<T>(c), c->d_td_chunks, c->n_td_chunks, c->nv,
+                                          (T)(a0 / dt), (T)(a1 / dt), (T)(a2 / dt), in[st], Un, Unm1,
+                                          (T*)c->d_H, s));
+    }
+    auto p = stage_params<T>(c);
+    p.job_range = c->d_job_range;
+    p.jobs = c->d_jobs;
+    p.job_bcs = c->d_job_bcs;
+    p.Uprev = in[st];
+    p.U0 = U;
+    p.Unext = out[st];
+    p.alpha = (T)alpha[st];
+    p.partials = (st == 0) ? c->d_partials : nullptr;
+    p.H = (const T*)c->d_H;
+    p.lam_v = (T)(a0 / dt);
+    hb_status r = stage_all<T>(c, p, 1, s);
+    if (r != HB_OK) return r;
+    if (st == 0)
+      for (size_t k = 0; k < c->cases.size(); ++k) {
+        const CaseHost& ch = c->cases[k];
+        c->n_launch++;
+        HB_CUDA(c, hbk::launch_norm_finish(c->d_partials + (size_t)8 * ch.tile0, ch.ntiles, c->nv,
+                                           1.0 / (double)ch.cells, norm_out + 8 * k, c->d_err, s));
+      }
+  }
+  return HB_OK;
+}
+
+template <typename T>
+hb_status td_step_impl(hb_ctx* c, T* U, const T* Un, const T* Unm1, double t, double dt, int n_inner,
+                       double* norms, cudaStream_t s) {
+  if (!c->d_td_chunks) {   // chunks of 128 padded cells over every block; H buffer
+    std::vector<int2> ch;
+    for (size_t b = 0; b < c->blocks.size(); ++b)
+      for (int64_t c0 = 0; c0 < c->blocks[b].plane; c0 += 128) ch.push_back(make_int2((int)b, (int)c0));
+    HB_CUDA(c, cudaMalloc(&c->d_td_chunks, sizeof(int2) * ch.size()));
+    HB_CUDA(c, cudaMemcpy(c->d_td_chunks, ch.data(), sizeof(int2) * ch.size(), cudaMemcpyHostToDevice));
+    c->n_td_chunks = (int)ch.size();
+    if (!c->d_H) HB_CUDA(c, cudaMalloc(&c->d_H, c->tsize * c->state_size));
+  }
+  // the cases' frame, grid velocity and inflow at time t
+  const size_t csz = sizeof(CaseDev<T>);
+  c->td_case_buf.resize(csz * c->cases.size());
+  for (size_t k = 0; k < c->cases.size(); ++k)
+    fill_case_dev<T>(c->cases[k], *(CaseDev<T>*)(c->td_case_buf.data() + csz * k), t);
+  HB_CUDA(c, cudaMemcpyAsync(c->d_cases, c->td_case_buf.data(), c->td_case_buf.size(), cudaMemcpyHostToDevice, s));
+  HB_CUDA(c, cudaStreamSynchronize(s));   // the host buffer is reused by the next step
+  hb_status r = halos<T>(c, U, s);
+  if (r != HB_OK) return r;
+  const size_t nc = c->cases.size();
+  int done = 0;
+  while (done < n_inner) {
+    const int K = std::min(n_inner - done, c->ring);
+    for (int k = 0; k < K; ++k) {
+      r = td_iteration<T>(c, U, Un, Unm1, dt, c->d_ring + 8 * nc * k, s);
+      if (r != HB_OK) return r;
+    }
+    r = copy_norms(c, norms, done, K, s);
+    if (r != HB_OK) return r;
+    done += K;
+  }
   return HB_OK;
 }
 
@@ -1796,6 +1886,20 @@ hb_status hb_load_state(hb_ctx* ctx, void* U, const char* path, int64_t* iterati
   cudaStream_t s = (cudaStream_t)stream;
   return ctx->prec == HB_FP32 ? load_impl<float>(ctx, (float*)U, path, iteration, s)
                               : load_impl<double>(ctx, (double*)U, path, iteration, s);
+}
+
+hb_status hb_td_step(hb_ctx* ctx, void* U, const void* U_n, const void* U_nm1, double t, double dt,
+                     int n_inner, double* norms, void* stream) {
+  if (!ctx || !U || !U_n || n_inner < 0 || !(dt > 0.0) || !(t >= 0.0))
+    return fail(ctx, HB_ERR_INVALID_ARG, "bad argument");
+  if (ctx->dim != 2 || ctx->ns_max != 1 || !ctx->jobs_ok)
+    return fail(ctx, HB_ERR_UNSUPPORTED, "time-domain stepping needs 2D cases with n_harm = 0");
+  if (n_inner == 0) return HB_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  return ctx->prec == HB_FP32
+             ? td_step_impl<float>(ctx, (float*)U, (const float*)U_n, (const float*)U_nm1, t, dt, n_inner, norms, s)
+             : td_step_impl<double>(ctx, (double*)U, (const double*)U_n, (const double*)U_nm1, t, dt, n_inner,
+                                    norms, s);
 }
 
 hb_status hb_sync_status(hb_ctx* ctx, void* stream) {

@@ -104,7 +104,8 @@ struct StageParams {
   double* partials;        // [ntiles][8] FP64 norm partials, or null
   T alpha;                 // RK stage coefficient
   int TI, TJ, ti_shift;    // tile shape; TI = 1 << ti_shift
-  const T* H;              // N_s > 9: HB source V omega D Uprev, same layout as the state
+  const T* H;              // N_s > 9: HB source V omega D Uprev; time-domain: the physical-time term
+  T lam_v;                 // time-domain: added to the spectral radius per unit volume (a0 / dt)
   const int2* job_range;   // RK mode: [ntiles] (first, count) into jobs, or null (no fused ghost fill)
   const GhostJob* jobs;
   const BcRec* job_bcs;
@@ -179,6 +180,11 @@ template <typename T>
 cudaError_t launch_forces(const ForceParams<T>& p, cudaStream_t s);
 template <typename T>
 cudaError_t launch_ghost_fill(const GhostFillParams<T>& p, cudaStream_t s);
+// time-domain physical-time term H = V (c0 U + c1 U_n + c2 U_nm1) over the
+// chunks (U_nm1 may be null), c_k = a_k / dt
+template <typename T>
+cudaError_t launch_td_source(const BlockDev* blocks, Geo<T> g, const int2* chunks, int nchunks, int nv, T c0,
+                             T c1, T c2, const T* U, const T* Un, const T* Unm1, T* H, cudaStream_t s);
 // H = V omega D U over the chunks (block, first padded cell) of 128 cells of
 // the blocks whose case has `ns` snapshots; D is that count's [ns][ns]
 // derivative matrix (host, FP64)

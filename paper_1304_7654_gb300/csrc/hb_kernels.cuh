@@ -413,6 +413,23 @@ __global__ void __launch_bounds__(kSrcCells) hb_source_kernel(const CaseDev<T>* 
   }
 }
 
+// Physical-time term of time-domain dual time stepping (second-order
+// backward differences): H = V (c0 U + c1 U_n + c2 U_nm1), per padded cell
+// and variable of one-snapshot blocks.
+template <typename T>
+__global__ void __launch_bounds__(kSrcCells) td_source_kernel(const BlockDev* blocks, Geo<T> g, const int2* chunks,
+                                                              T c0, T c1, T c2, const T* U, const T* Un,
+                                                              const T* Unm1, T* H) {
+  const int2 ck = chunks[blockIdx.x];
+  const BlockDev& B = blocks[ck.x];
+  const int64_t c = (int64_t)ck.y + threadIdx.x;
+  if (c >= B.plane) return;
+  const int64_t e = B.off + (int64_t)blockIdx.y * B.plane + c;
+  T u = c0 * U[e] + c1 * Un[e];
+  if (Unm1) u += c2 * Unm1[e];
+  H[e] = g.q[G_VOL][B.goff + c] * u;
+}
+
 // MODE 0: R := residual.  MODE 1: RK stage update (+ norm partials if set).
 // NS = 0: the snapshot count is the case's (large N_s); the HB source comes
 // from P.H and each snapshot is updated as soon as its face fluxes are known.
@@ -651,7 +668,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
       const T cv = (gam / C->prandtl > T(4.0 / 3.0)) ? gam / C->prandtl : T(4.0 / 3.0);
       lam += T(4) * cv * (mu * irho) * (ma2 + mb2) * iV;
     }
-    lam += omega * T(C->nh) * V;
+    lam += (omega * T(C->nh) + P.lam_v) * V;
     // dtau / V = cfl / lambda
     const T fac = P.alpha * C->cfl * Ar<T>::rcp(lam);
 #pragma unroll

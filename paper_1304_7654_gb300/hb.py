@@ -103,6 +103,7 @@ def load(path: str | None = None):
                                     ct.c_int]
     lib.hb_residual_norms_noalloc.argtypes = [_vp, _vp, ct.c_int, ct.c_int64, ct.c_int, ct.c_int,
                                               _vp, _vp]
+    lib.hb_td_step.argtypes = [_vp, _vp, _vp, _vp, ct.c_double, ct.c_double, ct.c_int, _vp, _vp]
     lib.hb_save_state.argtypes = [_vp, _vp, ct.c_char_p, ct.c_int64, _vp]
     lib.hb_load_state.argtypes = [_vp, _vp, ct.c_char_p, ct.POINTER(ct.c_int64), _vp]
     lib.hb_last_error.restype = ct.c_char_p
@@ -325,6 +326,21 @@ class HBContext:
         ms, n = ct.c_double(), ct.c_int64()
         self._check(self.lib.hb_kernel_stats(self.h, int(which), ct.byref(ms), ct.byref(n), int(reset)))
         return float(ms.value), int(n.value)
+
+    def td_step(self, U, U_n, U_nm1, t, dt, n_inner, norms=True):
+        """hb_td_step: n_inner dual-time iterations of the physical step to t
+        (BDF2; backward Euler when U_nm1 is None); returns FP64 norms
+        [n_inner][nv] (single case) or [n_inner][n_cases][nv]."""
+        import torch
+        nc = len(self.cases)
+        out = (torch.zeros((max(n_inner, 1), nc, self.nv), dtype=torch.float64, device=U.device)
+               if norms else None)
+        self._check(self.lib.hb_td_step(self.h, _ptr(U), _ptr(U_n), _ptr(U_nm1), float(t), float(dt),
+                                        int(n_inner), _ptr(out), _stream()))
+        if not norms:
+            return None
+        out = out[:n_inner]
+        return out[:, 0] if nc == 1 and not self.is_batch else out
 
     def save_state(self, U, path, iteration=0):
         """hb_save_state: restart file of U's interior cells with `iteration`."""
