@@ -528,10 +528,23 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   // Green-Gauss gradients of (u, v, T) at ring cell gq from buffer b, written
   // as sum (phi_nb - phi_c)/2 S over the closed cell (the faces sum to zero),
   // which keeps the rounding of large face vectors out of small cells
-  auto grad_cell = [&](int gq, const Fr<T>& f, int b) {
+  // work item w over the ring rows 0 .. rows-1: the TI inner columns of each
+  // row first (a warp reads one region row), then the two edge columns;
+  // gq is the ring cell's storage index in sG
+  const int ring_rows = tl.w + 2;
+  auto grad_cell = [&](int w, const Fr<T>& f, int b) {
     const T* W = sW + b * 4 * NR;
     const T* TT = sT + b * NR;
-    const int gi = gq % GI, gj = gq / GI;
+    int gi, gj;
+    if (w < TI * ring_rows) {
+      gi = w % TI + 1;
+      gj = w / TI;
+    } else {
+      const int k = w - TI * ring_rows;
+      gi = (k & 1) ? TI + 1 : 0;
+      gj = k >> 1;
+    }
+    const int gq = gj * GI + gi;
     const int r = (gj + 1) * RI + (gi + 1);
     const T uc = W[NR + r], vc = W[2 * NR + r], Tc = TT[r];
     T g[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
@@ -557,13 +570,22 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   };
 
   // one face of the tile from buffer b (faces no own cell uses are skipped)
-  auto face = [&](int fq, const Fr<T>& f, int b) {
+  // work item w: the first TI x TJ i-faces row by row, TI to a row (a warp
+  // reads one region row: no bank conflicts), then the TJ faces of column
+  // TI, then the j-faces; fq is the face's storage index in sF
+  auto face = [&](int w, const Fr<T>& f, int b) {
     const T* W = sW + b * 4 * NR;
     const T* TT = sT + b * NR;
-    int rL, st, d, gLi, gRi, fi, fj;
-    if (fq < NFI) {
-      fi = fq % (TI + 1);
-      fj = fq / (TI + 1);
+    int rL, st, d, gLi, gRi, fi, fj, fq = w;
+    if (w < NFI) {
+      if (w < TI * TJ) {
+        fi = w % TI;
+        fj = w / TI;
+      } else {
+        fi = TI;
+        fj = w - TI * TJ;
+      }
+      fq = fj * (TI + 1) + fi;
       if (i0 + fi > n0 || j0 + fj >= je) return;
       rL = (fj + 2) * RI + (fi + 1);
       st = 1;
