@@ -195,7 +195,7 @@ inline int64_t pcell(const BlockDev& B, int i, int j, int k) {
 // ------------------------------------------------------------ geometry --
 // static metrics of every padded cell, FP64, from the nodes (2 ghost layers)
 void compute_geometry(int dim, const hb_block_desc& bd, const BlockDev& B, std::vector<double>& G,
-                      int64_t geo_cells) {
+                      int64_t geo_cells, const double* pivot) {
   const int q0 = bd.ni + 5, q1 = bd.nj + 5;
   auto X = [&](int a, int b, int c, int comp) -> double {
     const int64_t idx = (dim == 3) ? (((int64_t)(c + 2) * q1 + (b + 2)) * q0 + (a + 2))
@@ -270,6 +270,21 @@ void compute_geometry(int dim, const hb_block_desc& bd, const BlockDev& B, std::
                 for (int e = 0; e < 2; ++e) s += X(i + a, j + b, k + e, m);
             put(hbk::G_XC + m, c, s / 8.0);
           }
+        }
+      }
+  // rigid pitch about the pivot: the grid velocity through a face, thdot *
+  // ((x_f - p) x S) / |S|, is frame independent (rotation keeps cross
+  // products), so the face's static factor is stored once
+  if (dim == 2)
+    for (int j = -2; j < B.n[1] + 2; ++j)
+      for (int i = -2; i < B.n[0] + 2; ++i) {
+        const int64_t c = pcell(B, i, j, 0);
+        for (int d = 0; d < 2; ++d) {
+          auto at = [&](int q) { return G[(size_t)q * geo_cells + B.goff + c]; };
+          const double sx = at(hbk::G_S + 3 * d), sy = at(hbk::G_S + 3 * d + 1);
+          const double ax = at(hbk::G_XF + 3 * d) - pivot[0], ay = at(hbk::G_XF + 3 * d + 1) - pivot[1];
+          const double a = std::sqrt(sx * sx + sy * sy);
+          put(hbk::G_VG + d, c, a > 0.0 ? (ax * sy - ay * sx) / a : 0.0);
         }
       }
   // centre differences, FP64 (keeps the face-normal distance exact to the
@@ -915,7 +930,7 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
   std::vector<double> G((size_t)hbk::G_NQ * ctx->geo_cells, 0.0);
   for (auto& ch : ctx->cases)
     for (int b = 0; b < ch.nblocks; ++b)
-      compute_geometry(ctx->dim, ch.d.blocks[b], ctx->blocks[ch.block0 + b], G, ctx->geo_cells);
+      compute_geometry(ctx->dim, ch.d.blocks[b], ctx->blocks[ch.block0 + b], G, ctx->geo_cells, ch.d.pivot);
   for (auto& ch : ctx->cases)
     for (int b = 0; b < ch.nblocks; ++b) {
       const BlockDev& B = ctx->blocks[ch.block0 + b];

@@ -49,7 +49,8 @@ enum {
   G_S = 4,             // S[d][comp]: low face of the cell along d, 9 arrays
   G_XF = 13,           // face centroid [d][comp], 9 arrays
   G_DC = 22,           // centre minus centre of the low neighbour along d [d][comp], 9 arrays
-  G_NQ = 31
+  G_VG = 31,           // 2D rigid pitch: ((x_f - pivot) x S) / |S| of the low face along d, 2 arrays
+  G_NQ = 33
 };
 
 struct CopyRec { int dst_blk, src_blk, dst_cell, src_cell; };

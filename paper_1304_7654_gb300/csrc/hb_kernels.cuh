@@ -615,13 +615,8 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
     }
     T sx, sy;
     rotv(f, sS[(2 * d) * NR + rR], sS[(2 * d + 1) * NR + rR], sx, sy);
-    T vgn = T(0);
-    if (moving) {
-      T xf, yf;
-      rotp(f, __ldg(P.g.q[G_XF + 3 * d] + gR), __ldg(P.g.q[G_XF + 3 * d + 1] + gR), xf, yf);
-      const T vgx = -f.thd * (yf - f.py), vgy = f.thd * (xf - f.px);
-      vgn = (vgx * sx + vgy * sy) * Ar<T>::rsq(sx * sx + sy * sy);
-    }
+    // normal grid velocity of the pitching face: thdot times its static factor
+    const T vgn = moving ? f.thd * __ldg(P.g.q[G_VG + d] + gR) : T(0);
     T F[4];
     roe2d(WL, WR, sx, sy, vgn, gm1, gg1, ig1, efix, efrac, F);
     if (VISC) {
