@@ -551,7 +551,12 @@ def run_profile(args):
     hbuild.build()
     from paper_1304_7654_gb300 import cases as C
     from paper_1304_7654_gb300 import hb
-    if args.profile_batch:
+    if args.profile_shape:
+        cs = C.paper_tc1() if args.profile_shape == "tc1" else C.paper_tc2()
+        ctx = hb.HBContext(cs, args.profile)
+        U = ctx.new_state()
+        ctx.init_state(U, torch.as_tensor(C.noise(cs), device="cuda"), 0.01)
+    elif args.profile_batch:
         import numpy as np
         cases = C.batch_cases()
         ctx = hb.HBContext(cases, args.profile)
@@ -568,7 +573,7 @@ def run_profile(args):
         ctx.set_tuning(mode, ti, tj)
     norms = torch.zeros((1, cs.nv), dtype=torch.float64, device="cuda")
     for _ in range(args.warmup + args.steps):
-        if args.profile_batch:
+        if args.profile_batch or args.profile_shape:
             ctx.rk_smooth_into(U, 1, None)
         else:
             ctx.rk_smooth_into(U, 1, norms)
@@ -592,6 +597,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--profile", choices=["fp32", "fp64"], default=None)
     ap.add_argument("--profile-batch", action="store_true")
+    ap.add_argument("--profile-shape", default=None, choices=["tc1", "tc2"],
+                    help="with --profile: the paper-shaped workload instead of the 8-block O-grid")
     ap.add_argument("--tuning", default=None,
                     help="mode,TI,TJ (0 per-phase, 1 persistent; +2 separate halo passes instead of the fused ghost fill)")
     args = ap.parse_args()
