@@ -298,6 +298,29 @@ hb_status hb_load_state(hb_ctx* ctx, void* U, const char* path, int64_t* iterati
 hb_status hb_td_step(hb_ctx* ctx, void* U, const void* U_n, const void* U_nm1, double t, double dt,
                      int n_inner, double* norms, void* stream);
 
+/* FP32 smoothing with an FP64 finish (defect correction): for an FP32 and an
+ * FP64 context of the same 2D cases (N_H up to HB_MAX_STATIC_HARMONICS) and
+ * an FP64 state U64 (device, ctx64's layout, e.g. a converged FP32 state cast
+ * up), n_outer times: the FP64 residual r = R64(U64) and the FP32 residual of
+ * u = (float) U64 are formed, the scaled correction equation
+ *     R32(u + e) + (sigma r - R32(u)) = 0
+ * is smoothed from e = 0 by n_inner FP32 RK iterations (one launch per
+ * phase), and U64 += e / sigma in FP64.  The fixed point is R64(U64) = 0, so
+ * the converged state and forces become the FP64 solution's (the FP32 target
+ * on converged force coefficients).  sigma > 0 scales the correction so that
+ * the FP32 state u + e resolves it: FP32 keeps about 7 digits of u, and the
+ * FP32-converged state differs from the FP64 one by ~1e-6 |u|, so sigma of
+ * order 1e4 is needed; each outer iteration then removes the defect down to
+ * the linearisation error of e (sigma = 1 leaves the FP32 error in place).
+ * norms (device, may be NULL): [n_outer][n_cases][nv] FP64 RMS over interior
+ * cells and snapshots of (R32(u) + sigma r - R32(u)) / V at the first
+ * correction iteration, i.e. sigma times the FP64 defect through FP32.
+ * Errors: HB_ERR_INVALID_ARG (null pointers, negative counts, sigma <= 0,
+ * contexts of other precisions or other cases), HB_ERR_UNSUPPORTED (N_H
+ * above HB_MAX_STATIC_HARMONICS).  Asynchronous on `stream`. */
+hb_status hb_defect_correction(hb_ctx* ctx32, hb_ctx* ctx64, void* U64, int n_outer, int n_inner, double sigma,
+                               double* norms, void* stream);
+
 /* Synchronise `stream`, then read and clear the device error word. */
 hb_status hb_sync_status(hb_ctx* ctx, void* stream);
 

@@ -98,6 +98,8 @@ struct hb_ctx {
   int2* d_td_chunks = nullptr;
   int n_td_chunks = 0;
   std::vector<unsigned char> td_case_buf;
+  // defect correction workspace (FP32 context: u32, v32, r32, src; FP64 context: r64)
+  void* d_dc[4] = {nullptr, nullptr, nullptr, nullptr};
   int n_bodies = 0;
   void* d_A = nullptr;          // RK ping-pong and residual scratch
   void* d_B = nullptr;
@@ -594,6 +596,7 @@ void free_ctx(hb_ctx* c) {
   cudaFree(c->d_chunks);
   cudaFree(c->d_H);
   cudaFree(c->d_td_chunks);
+  for (int k = 0; k < 4; ++k) cudaFree(c->d_dc[k]);
   cudaFree(c->d_A);
   cudaFree(c->d_B);
   cudaFree(c->d_partials);
@@ -1253,7 +1256,7 @@ hb_status residual_impl(hb_ctx* c, const T* U, T* R, cudaStream_t s) {
 
 // one RK iteration; norms (nv doubles per case block of 8) written to `norm_out`
 template <typename T>
-hb_status rk_iteration(hb_ctx* c, T* U, double* norm_out, cudaStream_t s) {
+hb_status rk_iteration(hb_ctx* c, T* U, double* norm_out, cudaStream_t s, const T* src = nullptr) {
   static const double alpha[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
   T* A = (T*)c->d_A;
   T* Bf = (T*)c->d_B;
@@ -1277,6 +1280,7 @@ hb_status rk_iteration(hb_ctx* c, T* U, double* norm_out, cudaStream_t s) {
     r = hb_source<T>(c, in[st], s);
     if (r != HB_OK) return r;
     if (c->large_ns()) p.H = (const T*)c->d_H;
+    p.src = src;
     r = stage_all<T>(c, p, 1, s);
     if (r != HB_OK) return r;
     if (st == 0) {
@@ -1711,6 +1715,56 @@ hb_status load_impl(hb_ctx* c, T* U, const char* path, int64_t* it, cudaStream_t
 }
 }  // namespace
 
+// ---- FP32 smoothing with an FP64 finish (defect correction)
+namespace {
+uint64_t ctx_signature_any_precision(const hb_ctx* c) {
+  hb_ctx tmp;   // only the fields the signature reads
+  tmp.dim = c->dim;
+  tmp.prec = 0;
+  tmp.cases = c->cases;
+  tmp.blocks = c->blocks;
+  return ctx_signature(&tmp);
+}
+
+hb_status defect_impl(hb_ctx* c32, hb_ctx* c64, double* U64, int n_outer, int n_inner, double sigma,
+                      double* norms, cudaStream_t s) {
+  const int64_t n = c32->state_size;
+  for (int k = 0; k < 4; ++k)
+    if (!c32->d_dc[k]) HB_CUDA(c32, cudaMalloc(&c32->d_dc[k], sizeof(float) * n));
+  if (!c64->d_dc[0]) HB_CUDA(c64, cudaMalloc(&c64->d_dc[0], sizeof(double) * n));
+  float* u32 = (float*)c32->d_dc[0];
+  float* v32 = (float*)c32->d_dc[1];
+  float* r32 = (float*)c32->d_dc[2];
+  float* src = (float*)c32->d_dc[3];
+  double* r64 = (double*)c64->d_dc[0];
+  const size_t nc = c32->cases.size();
+  HB_CUDA(c32, cudaMemsetAsync(r32, 0, sizeof(float) * n, s));
+  HB_CUDA(c64, cudaMemsetAsync(r64, 0, sizeof(double) * n, s));
+  for (int it = 0; it < n_outer; ++it) {
+    // the FP64 defect of the current state and the FP32 residual of its rounding
+    hb_status r = residual_impl<double>(c64, U64, r64, s);
+    if (r != HB_OK) return r;
+    HB_CUDA(c32, hbk::launch_cast_down(U64, u32, n, s));
+    r = residual_impl<float>(c32, u32, r32, s);
+    if (r != HB_OK) return r;
+    HB_CUDA(c32, hbk::launch_defect_source(r64, r32, src, sigma, n, s));
+    // smooth R32(u32 + d) + (r64 - R32(u32)) = 0 from d = 0 in FP32, then u64 += d
+    HB_CUDA(c32, cudaMemcpyAsync(v32, u32, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+    r = halos<float>(c32, v32, s);
+    if (r != HB_OK) return r;
+    for (int k = 0; k < n_inner; ++k) {
+      r = rk_iteration<float>(c32, v32, c32->d_ring + (k == 0 ? 0 : 8 * nc), s, src);
+      if (r != HB_OK) return r;
+    }
+    HB_CUDA(c32, hbk::launch_defect_update(U64, v32, u32, sigma, n, s));
+    if (norms && n_inner > 0)
+      HB_CUDA(c32, cudaMemcpy2DAsync(norms + (size_t)it * nc * c32->nv, sizeof(double) * c32->nv, c32->d_ring,
+                                     sizeof(double) * 8, sizeof(double) * c32->nv, nc, cudaMemcpyDeviceToDevice, s));
+  }
+  return HB_OK;
+}
+}  // namespace
+
 extern "C" {
 
 hb_status hb_create(const hb_case_desc* desc, hb_ctx** out) { return create_impl(desc, 1, out); }
@@ -1915,6 +1969,18 @@ hb_status hb_td_step(hb_ctx* ctx, void* U, const void* U_n, const void* U_nm1, d
              ? td_step_impl<float>(ctx, (float*)U, (const float*)U_n, (const float*)U_nm1, t, dt, n_inner, norms, s)
              : td_step_impl<double>(ctx, (double*)U, (const double*)U_n, (const double*)U_nm1, t, dt, n_inner,
                                     norms, s);
+}
+
+hb_status hb_defect_correction(hb_ctx* ctx32, hb_ctx* ctx64, void* U64, int n_outer, int n_inner, double sigma,
+                               double* norms, void* stream) {
+  if (!ctx32 || !ctx64 || !U64 || n_outer < 0 || n_inner < 0 || !(sigma > 0.0))
+    return fail(ctx32, HB_ERR_INVALID_ARG, "bad argument");
+  if (ctx32->prec != HB_FP32 || ctx64->prec != HB_FP64 || ctx32->dim != 2 ||
+      ctx32->state_size != ctx64->state_size ||
+      ctx_signature_any_precision(ctx32) != ctx_signature_any_precision(ctx64))
+    return fail(ctx32, HB_ERR_INVALID_ARG, "defect correction needs an FP32 and an FP64 context of the same 2D cases");
+  if (ctx32->large_ns()) return fail(ctx32, HB_ERR_UNSUPPORTED, "defect correction: n_harm above HB_MAX_STATIC_HARMONICS");
+  return defect_impl(ctx32, ctx64, (double*)U64, n_outer, n_inner, sigma, norms, (cudaStream_t)stream);
 }
 
 hb_status hb_sync_status(hb_ctx* ctx, void* stream) {

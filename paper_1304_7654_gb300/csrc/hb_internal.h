@@ -107,6 +107,7 @@ struct StageParams {
   int TI, TJ, ti_shift;    // tile shape; TI = 1 << ti_shift
   const T* H;              // N_s > 9: HB source V omega D Uprev; time-domain: the physical-time term
   T lam_v;                 // time-domain: added to the spectral radius per unit volume (a0 / dt)
+  const T* src;            // RK mode: a fixed source added to the residual (defect correction), or null
   const int2* job_range;   // RK mode: [ntiles] (first, count) into jobs, or null (no fused ghost fill)
   const GhostJob* jobs;
   const BcRec* job_bcs;
@@ -212,6 +213,13 @@ bool persist_available(int TI, int TJ);
 
 cudaError_t launch_norm_finish(const double* partials, int ntiles, int nv, double inv_count,
                                double* out, int* err, cudaStream_t s);
+// defect correction, elementwise over n state entries: u32 = (float) u64;
+// src = (float)(sigma r64 - r32); u64 += (v32 - u32) / sigma (in FP64)
+cudaError_t launch_cast_down(const double* u64, float* u32, int64_t n, cudaStream_t s);
+cudaError_t launch_defect_source(const double* r64, const float* r32, float* src, double sigma, int64_t n,
+                                 cudaStream_t s);
+cudaError_t launch_defect_update(double* u64, const float* v32, const float* u32, double sigma, int64_t n,
+                                 cudaStream_t s);
 cudaError_t launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t s);
 
 }  // namespace hbk

@@ -653,8 +653,12 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   for (int q = 0; q < NV; ++q) tacc[q] = T(0);
   // residual Rn of the own cell at snapshot n -> R, or the RK update of U0
   // with the local time step (and the norm partial)
-  auto finish = [&](int n, const T* Rn) {
+  auto finish = [&](int n, T* Rn) {
     const int64_t base = B.off + (int64_t)n * NV * B.plane + cown;
+    if (MODE == 1 && P.src) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) Rn[q] += P.src[base + q * B.plane];
+    }
     if (MODE == 0) {
 #pragma unroll
       for (int q = 0; q < NV; ++q) P.R[base + q * B.plane] = Rn[q];

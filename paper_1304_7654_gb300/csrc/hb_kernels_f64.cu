@@ -39,6 +39,45 @@ __global__ void copy_kernel(const uint4* __restrict__ src, uint4* __restrict__ d
     dst[e] = src[e];
 }
 
+__global__ void cast_down_kernel(const double* __restrict__ u64, float* __restrict__ u32, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    u32[e] = (float)u64[e];
+}
+
+__global__ void defect_source_kernel(const double* __restrict__ r64, const float* __restrict__ r32,
+                                     float* __restrict__ src, double sigma, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    src[e] = (float)(sigma * r64[e] - (double)r32[e]);
+}
+
+__global__ void defect_update_kernel(double* __restrict__ u64, const float* __restrict__ v32,
+                                     const float* __restrict__ u32, double inv_sigma, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    u64[e] += ((double)v32[e] - (double)u32[e]) * inv_sigma;
+}
+
+static unsigned elementwise_grid(int64_t n) {
+  int64_t nb = (n + 255) / 256;
+  return (unsigned)(nb > 152 * 16 ? 152 * 16 : (nb < 1 ? 1 : nb));
+}
+
+cudaError_t launch_cast_down(const double* u64, float* u32, int64_t n, cudaStream_t s) {
+  cast_down_kernel<<<elementwise_grid(n), 256, 0, s>>>(u64, u32, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_defect_source(const double* r64, const float* r32, float* src, double sigma, int64_t n,
+                                 cudaStream_t s) {
+  defect_source_kernel<<<elementwise_grid(n), 256, 0, s>>>(r64, r32, src, sigma, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_defect_update(double* u64, const float* v32, const float* u32, double sigma, int64_t n,
+                                 cudaStream_t s) {
+  defect_update_kernel<<<elementwise_grid(n), 256, 0, s>>>(u64, v32, u32, 1.0 / sigma, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t s) {
   if (bytes % 16 != 0) return cudaErrorInvalidValue;
   int64_t n16 = bytes / 16;

@@ -104,6 +104,7 @@ def load(path: str | None = None):
     lib.hb_residual_norms_noalloc.argtypes = [_vp, _vp, ct.c_int, ct.c_int64, ct.c_int, ct.c_int,
                                               _vp, _vp]
     lib.hb_td_step.argtypes = [_vp, _vp, _vp, _vp, ct.c_double, ct.c_double, ct.c_int, _vp, _vp]
+    lib.hb_defect_correction.argtypes = [_vp, _vp, _vp, ct.c_int, ct.c_int, ct.c_double, _vp, _vp]
     lib.hb_save_state.argtypes = [_vp, _vp, ct.c_char_p, ct.c_int64, _vp]
     lib.hb_load_state.argtypes = [_vp, _vp, ct.c_char_p, ct.POINTER(ct.c_int64), _vp]
     lib.hb_last_error.restype = ct.c_char_p
@@ -340,6 +341,21 @@ class HBContext:
         if not norms:
             return None
         out = out[:n_inner]
+        return out[:, 0] if nc == 1 and not self.is_batch else out
+
+    def defect_correction(self, ctx64, U64, n_outer, n_inner, sigma=1.0, norms=True):
+        """hb_defect_correction with this FP32 context and the FP64 context
+        ctx64 of the same case(s): U64 (FP64 state) refined in place; returns
+        the FP64 defect norms [n_outer][nv] (single case) or [n_outer][n_cases][nv]."""
+        import torch
+        nc = len(self.cases)
+        out = (torch.zeros((max(n_outer, 1), nc, self.nv), dtype=torch.float64, device=U64.device)
+               if norms else None)
+        self._check(self.lib.hb_defect_correction(self.h, ctx64.h, _ptr(U64), int(n_outer), int(n_inner),
+                                                  float(sigma), _ptr(out), _stream()))
+        if not norms:
+            return None
+        out = out[:n_outer]
         return out[:, 0] if nc == 1 and not self.is_batch else out
 
     def save_state(self, U, path, iteration=0):
