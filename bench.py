@@ -161,6 +161,24 @@ def cpu_baseline():
 
 
 # --------------------------------------------------------------- our arm --
+def max_over_ranks(values, dev):
+    """Element-wise maximum of a list of floats over the ranks of the default
+    process group (the values themselves on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def replica_throughput(world_size, units_per_rank_step, ms_per_step):
+    """Whole-job throughput of independent replicas: every rank's units over
+    the slowest rank's step time."""
+    return world_size * units_per_rank_step / (ms_per_step * 1e-3)
+
+
 def algorithmic_bytes_per_unit(nv, s, moving, viscous, ns):
     """Bytes one cell-snapshot-stage must move, averaged over the 4 stages:
     stage 1 reads U and writes U1 (2 nv s); stages 2-4 read U^(s-1), U^(0) and
@@ -318,17 +336,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_ms = sum(a.elapsed_time(b) for a, b in evs) / e2e_steps
 
-    # max over ranks
-    ms32 = r32["ms"]
-    if ws > 1:
-        t = torch.tensor([ms32], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms32 = float(t.item())
-        te = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e_ms = float(te.item())
+    # max over ranks; every rank ran its own replica of the workload
+    ms32, e2e_ms = max_over_ranks([r32["ms"], e2e_ms], dev)
     ms_per_step = ms32 / args.steps
-    value = ws * units_per_step / (ms_per_step * 1e-3)
+    value = replica_throughput(ws, units_per_step, ms_per_step)
     v64 = units_per_step / (r64["ms"] / args.fp64_steps * 1e-3)
 
     peaks, src = _peaks()
