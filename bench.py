@@ -184,9 +184,9 @@ def algorithmic_bytes_per_unit(nv, s, moving, viscous, ns):
     stage 1 reads U and writes U1 (2 nv s); stages 2-4 read U^(s-1), U^(0) and
     write (3 nv s); plus the static metrics each stage reads once per cell for
     all snapshots: volume, 2 face vectors (4), centre differences (4, viscous),
-    face midpoints (4) and centre (2) (moving grids)."""
+    the faces' grid-velocity factors (2) and the centre (2) (pitching grids)."""
     state = (2 + 3 + 3 + 3) / 4.0 * nv * s
-    geo = 1 + 4 + (4 if viscous else 0) + (6 if moving else 0)
+    geo = 1 + 4 + (4 if viscous else 0) + (4 if moving else 0)
     return state + geo * s / ns
 
 
