@@ -359,6 +359,8 @@ def run_ours(args):
                            l2="flushed between timed steps (512 MB write, not timed)",
                            step="1 RK iteration (4 stages) + force reduction"),
             "roofline": roof,
+            "roofline_alu": alu_roofline(f"{'persist' if mode & 1 else 'tile2d'}_f32_{TI}x{TJ}_ns_ogrid8",
+                                         cs.n_cells * cs.n_snap * (4 if mode & 1 else 1), launch_ms),
             "e2e": {"value": ws * units_per_step / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": int(host_U.numel() * host_U.element_size()),
                     "d2h_bytes_per_step": int(host_out.numel() * host_out.element_size())},
@@ -536,6 +538,38 @@ def adjoint_ratio(dev):
     ta = timed(lambda: ctx.adjoint_residual(U, psi, 0.5, r))
     return {"primal_ms": tp, "adjoint_ms": ta, "ratio": ta / tp,
             "workload": "adjoint_ogrid4: 4 blocks, 512x256 cells, N_H=4, laminar, FP64"}
+
+
+def _profile_record(name):
+    """The committed ncu record of a kernel (profiles/traffic.json), if it was
+    taken on the current kernel source, else None."""
+    try:
+        import hashlib
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[name]
+        src = b"".join(open(os.path.join(ROOT, "paper_1304_7654_gb300", "csrc", n), "rb").read()
+                       for n in rec.get("sources", ["hb_kernels.cuh"]))
+        return rec if rec.get("kernel_sha1") == hashlib.sha1(src).hexdigest() else None
+    except Exception:
+        return None
+
+
+# FP32 FMA-pipe peak from the unit counts and clock: 152 SMs x 128 lanes x 2 flops x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def alu_roofline(name, units, launch_ms):
+    """The tile kernel against the FP32 arithmetic roof: executed FP32 flops
+    per cell-snapshot-stage from the committed ncu record, over the measured
+    launch time."""
+    rec = _profile_record(name)
+    if not rec or "fp32_flops_per_unit" not in rec or launch_ms <= 0:
+        return None
+    achieved = rec["fp32_flops_per_unit"] * units / (launch_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "flops_per_unit": rec["fp32_flops_per_unit"],
+            "flops_source": "executed FP32 operations per cell-snapshot-stage (FFMA counted twice), ncu",
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
 
 
 def _traffic_record(name):
