@@ -111,8 +111,10 @@ def _cpu_cores():
 # ------------------------------------------------------------ reference arm --
 def run_reference(args):
     """FP64 CPU oracle as it stands, single thread: each step is one RK
-    iteration of the same 8-block NS O-grid family at 320 x 48 cells (1/16 of
-    the cells: a bounded sample), timed on the host clock."""
+    iteration of the same 8-block NS O-grid family on a bounded sample of the
+    cells (320 x 48, or 160 x 48 / 80 x 48 when that many steps would take
+    more than about two minutes at ~0.6 s per 320 x 48 step), timed on the
+    host clock."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
@@ -120,7 +122,10 @@ def run_reference(args):
     from oracle.hb_oracle import Oracle, build
     from paper_1304_7654_gb300 import cases as C
     build()
-    cs = C.ns_ogrid8(320, 48)
+    ni = 320
+    while ni > 80 and (args.steps + args.warmup) * 0.65 * ni / 320 > 120:
+        ni //= 2
+    cs = C.ns_ogrid8(ni, 48)
     o = Oracle(cs)
     U = o.init_state(C.noise(cs), 0.01)
     for _ in range(args.warmup):
@@ -131,7 +136,7 @@ def run_reference(args):
     dt = time.perf_counter() - t
     units = cs.n_cells * cs.n_snap * 4 * args.steps
     val = units / dt
-    sample = ("one RK iteration per step of the ns_ogrid8 family at 320x48 cells (15,360 cells, "
+    sample = (f"one RK iteration per step of the ns_ogrid8 family at {ni}x48 cells ({cs.n_cells:,} cells, "
               "N_H=3), single-threaded FP64 oracle")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
