@@ -17,7 +17,10 @@
  *   - Force coefficients cl, cd (and cm when functag == 3) per body and
  *     snapshot, aggregated into one reduction per RK step packed
  *     [snapshot][body][cl,cd,cm]: Sec. 3.1 -> hb_forces.
- *   - Restart data and per-snapshot output: Sec. 3.1 (not part of this ABI).
+ *   - Restart file: Sec. 3.1 -> hb_save_state / hb_load_state (per-snapshot
+ *     visualisation output is not part of this ABI).
+ *   - The two test cases (31 and 17 snapshots, 512 and 2048 blocks):
+ *     Sec. 4.1 -> HB_MAX_HARMONICS.
  * The scheme itself (flux, limiter, RK, time step, boundary conditions) is
  * not printed in the paper; the readings used are documented beside each
  * kernel in the sources.

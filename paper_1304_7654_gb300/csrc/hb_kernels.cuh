@@ -14,14 +14,17 @@
 //   * local time step CFL V / (sum_d (|u_rel . S_d| + c|S_d|) + viscous
 //     + omega N_H V), 4-stage RK U^(s) = U^(0) - alpha_s dtau/V R(U^(s-1)).
 //
-// Tile kernel layout: one CTA owns a TI x TJ tile of one block and loops over
-// all snapshots; per snapshot it stages the primitives of the tile plus a
-// 2-cell halo in shared memory, computes Green-Gauss gradients on a 1-cell
-// ring, then every face flux of the tile exactly once, and accumulates the
-// flux balance of each own cell into registers.  The HB source needs the own
-// cell at all snapshots: it is accumulated as each snapshot passes, so the
-// state is read once per stage.  Registers hold acc[NS][NV] (flux balance)
-// and h[NS][NV] (D.U) as shift registers indexed at compile time.
+// Tile kernel layout: one CTA owns a TI x TJ tile (or a row strip of one) of
+// one block and loops over all snapshots; per snapshot it stages the
+// primitives of the tile plus a 2-cell halo in shared memory (double-buffered:
+// the next snapshot is staged while this one's faces run), computes
+// Green-Gauss gradients on a 1-cell ring, then every face flux of the tile
+// exactly once, and keeps the flux balance of each own cell per snapshot in
+// shared memory.  The epilogue adds the HB source, which needs the own cell
+// at all snapshots (read once per stage), and updates every snapshot; the
+// tile then writes the ghost cells its own cells feed (fused halo fill).  With
+// more than 9 snapshots the HB source comes precomputed from its own launch
+// and each snapshot is updated as soon as its fluxes are known.
 #pragma once
 
 #include <cuda_runtime.h>
