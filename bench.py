@@ -545,16 +545,29 @@ def adjoint_ratio(dev):
             "workload": "adjoint_ogrid4: 4 blocks, 512x256 cells, N_H=4, laminar, FP64"}
 
 
+def kernel_source_hash(names):
+    """SHA-1 of the kernel sources' code: comments removed and whitespace
+    collapsed, so that an edited comment does not orphan a profile record."""
+    import hashlib
+    import re
+    text = ""
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1304_7654_gb300", "csrc", n)) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        text += " ".join(src.split()) + "\n"
+    return hashlib.sha1(text.encode()).hexdigest()
+
+
 def _profile_record(name):
     """The committed ncu record of a kernel (profiles/traffic.json), if it was
     taken on the current kernel source, else None."""
     try:
-        import hashlib
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f)[name]
-        src = b"".join(open(os.path.join(ROOT, "paper_1304_7654_gb300", "csrc", n), "rb").read()
-                       for n in rec.get("sources", ["hb_kernels.cuh"]))
-        return rec if rec.get("kernel_sha1") == hashlib.sha1(src).hexdigest() else None
+        ok = rec.get("kernel_sha1") == kernel_source_hash(rec.get("sources", ["hb_kernels.cuh"]))
+        return rec if ok else None
     except Exception:
         return None
 
@@ -580,17 +593,8 @@ def alu_roofline(name, units, launch_ms):
 def _traffic_record(name):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
-    try:
-        import hashlib
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            rec = json.load(f)[name]
-        src = b"".join(open(os.path.join(ROOT, "paper_1304_7654_gb300", "csrc", n), "rb").read()
-                       for n in rec.get("sources", ["hb_kernels.cuh"]))
-        if rec.get("kernel_sha1") != hashlib.sha1(src).hexdigest():
-            return None
-        return rec["dram_bytes_per_launch"]
-    except Exception:
-        return None
+    rec = _profile_record(name)
+    return rec["dram_bytes_per_launch"] if rec else None
 
 
 def run_profile(args):
