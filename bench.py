@@ -606,7 +606,7 @@ def run_profile(args):
     from paper_1304_7654_gb300 import cases as C
     from paper_1304_7654_gb300 import hb
     if args.profile_shape:
-        cs = C.paper_tc1() if args.profile_shape == "tc1" else C.paper_tc2()
+        cs = {"tc1": C.paper_tc1, "tc2": C.paper_tc2, "box3d": C.box3d}[args.profile_shape]()
         ctx = hb.HBContext(cs, args.profile)
         U = ctx.new_state()
         ctx.init_state(U, torch.as_tensor(C.noise(cs), device="cuda"), 0.01)
@@ -651,8 +651,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--profile", choices=["fp32", "fp64"], default=None)
     ap.add_argument("--profile-batch", action="store_true")
-    ap.add_argument("--profile-shape", default=None, choices=["tc1", "tc2"],
-                    help="with --profile: the paper-shaped workload instead of the 8-block O-grid")
+    ap.add_argument("--profile-shape", default=None, choices=["tc1", "tc2", "box3d"],
+                    help="with --profile: a paper-shaped workload or the 3D box instead of the 8-block O-grid")
     ap.add_argument("--tuning", default=None,
                     help="mode,TI,TJ (0 per-phase, 1 persistent; +2 separate halo passes instead of the fused ghost fill)")
     args = ap.parse_args()
