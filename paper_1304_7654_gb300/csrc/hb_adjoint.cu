@@ -56,13 +56,7 @@ __device__ __forceinline__ void prim4_adj(const T* W, T Tbar, const T* Wb_in, T 
   Ub[3] = Wb[3] * gm1;
 }
 
-// conservative from primitive and its adjoint (Ubar -> Wbar)
-__device__ __forceinline__ void cons4(const T* W, T ig1, T* U) {
-  U[0] = W[0];
-  U[1] = W[0] * W[1];
-  U[2] = W[0] * W[2];
-  U[3] = W[3] * ig1 + 0.5 * W[0] * (W[1] * W[1] + W[2] * W[2]);
-}
+// adjoint of conservative-from-primitive (Ubar -> Wbar)
 __device__ __forceinline__ void cons4_adj(const T* W, const T* Ub, T ig1, T* Wb) {
   const T k = 0.5 * (W[1] * W[1] + W[2] * W[2]);
   Wb[0] = Ub[0] + Ub[1] * W[1] + Ub[2] * W[2] + Ub[3] * k;

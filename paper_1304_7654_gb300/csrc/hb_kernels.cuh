@@ -662,46 +662,46 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
 #pragma unroll
       for (int q = 0; q < NV; ++q) Rn[q] += P.src[base + q * B.plane];
     }
-    if (MODE == 0) {
+    if constexpr (MODE == 0) {
 #pragma unroll
       for (int q = 0; q < NV; ++q) P.R[base + q * B.plane] = Rn[q];
-      return;
-    }
-    T u0[NV];
+    } else {
+      T u0[NV];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) u0[q] = P.U0[base + q * B.plane];
-    const Fr<T> f = frame_at(C, n);
-    const T rho = u0[0], irho = Ar<T>::rcp(rho);
-    const T uv = u0[1] * irho, vv = u0[2] * irho;
-    const T pp = gm1 * (u0[3] - T(0.5) * rho * (uv * uv + vv * vv));
-    const T c2 = gam * pp * irho;
-    const T cs = c2 * Ar<T>::rsq(c2);
-    T urx = uv, ury = vv;
-    if (moving) {
-      T xc, yc;
-      rotp(f, P.g.q[G_XC][B.goff + cown], P.g.q[G_XC + 1][B.goff + cown], xc, yc);
-      urx -= -f.thd * (yc - f.py);
-      ury -= f.thd * (xc - f.px);
-    }
-    T ax, ay, bx, by;
-    rotv(f, a0x, a0y, ax, ay);
-    rotv(f, b0x, b0y, bx, by);
-    const T ma = ma2 * Ar<T>::rsq(ma2), mb = mb2 * Ar<T>::rsq(mb2);
-    T lam = fabs(urx * ax + ury * ay) + cs * ma + fabs(urx * bx + ury * by) + cs * mb;
-    if (VISC) {
-      const T cv = (gam / C->prandtl > T(4.0 / 3.0)) ? gam / C->prandtl : T(4.0 / 3.0);
-      lam += T(4) * cv * (mu * irho) * (ma2 + mb2) * iV;
-    }
-    lam += (omega * T(C->nh) + P.lam_v) * V;
-    // dtau / V = cfl / lambda
-    const T fac = P.alpha * C->cfl * Ar<T>::rcp(lam);
+      for (int q = 0; q < NV; ++q) u0[q] = P.U0[base + q * B.plane];
+      const Fr<T> f = frame_at(C, n);
+      const T rho = u0[0], irho = Ar<T>::rcp(rho);
+      const T uv = u0[1] * irho, vv = u0[2] * irho;
+      const T pp = gm1 * (u0[3] - T(0.5) * rho * (uv * uv + vv * vv));
+      const T c2 = gam * pp * irho;
+      const T cs = c2 * Ar<T>::rsq(c2);
+      T urx = uv, ury = vv;
+      if (moving) {
+        T xc, yc;
+        rotp(f, P.g.q[G_XC][B.goff + cown], P.g.q[G_XC + 1][B.goff + cown], xc, yc);
+        urx -= -f.thd * (yc - f.py);
+        ury -= f.thd * (xc - f.px);
+      }
+      T ax, ay, bx, by;
+      rotv(f, a0x, a0y, ax, ay);
+      rotv(f, b0x, b0y, bx, by);
+      const T ma = ma2 * Ar<T>::rsq(ma2), mb = mb2 * Ar<T>::rsq(mb2);
+      T lam = fabs(urx * ax + ury * ay) + cs * ma + fabs(urx * bx + ury * by) + cs * mb;
+      if (VISC) {
+        const T cv = (gam / C->prandtl > T(4.0 / 3.0)) ? gam / C->prandtl : T(4.0 / 3.0);
+        lam += T(4) * cv * (mu * irho) * (ma2 + mb2) * iV;
+      }
+      lam += (omega * T(C->nh) + P.lam_v) * V;
+      // dtau / V = cfl / lambda
+      const T fac = P.alpha * C->cfl * Ar<T>::rcp(lam);
 #pragma unroll
-    for (int q = 0; q < NV; ++q) P.Unext[base + q * B.plane] = u0[q] - fac * Rn[q];
-    if (P.partials) {
+      for (int q = 0; q < NV; ++q) P.Unext[base + q * B.plane] = u0[q] - fac * Rn[q];
+      if (P.partials) {
 #pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        const T x = Rn[q] * iV;
-        tacc[q] += x * x;
+        for (int q = 0; q < NV; ++q) {
+          const T x = Rn[q] * iV;
+          tacc[q] += x * x;
+        }
       }
     }
   };
