@@ -136,7 +136,7 @@ struct ForceParams {
   const BcRec* walls;
   int nwall;
   int ns;
-  double* face_out;         // [nwall][ns][3]
+  double* face_out;         // [ns][nwall][3]
   double* coef;             // [ns][nbodies][3] or null
   double* J;                // or null
   int nbodies;

@@ -952,7 +952,8 @@ template <typename T>
 __global__ void force_faces_kernel(ForceParams<T> p) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= p.nwall * p.ns) return;
-  const int rec = gid / p.ns, n = gid % p.ns;
+  // consecutive threads take consecutive wall faces of one snapshot
+  const int n = gid / p.nwall, rec = gid % p.nwall;
   const BcRec r = p.walls[rec];
   const BlockDev B = p.blocks[r.blk];
   const CaseDev<T>* C = p.cases + B.cs;
@@ -995,7 +996,7 @@ __global__ void force_faces_kernel(ForceParams<T> p) {
     Fy -= sg * Fv[2];
   }
   const double q = 0.5 * (double)C->mach * (double)C->mach;
-  double* o = p.face_out + ((int64_t)rec * p.ns + n) * 3;
+  double* o = p.face_out + ((int64_t)n * p.nwall + rec) * 3;
   o[0] = ((double)Fx * (double)-C->sina0 + (double)Fy * (double)C->cosa0) / q;
   o[1] = ((double)Fx * (double)C->cosa0 + (double)Fy * (double)C->sina0) / q;
   o[2] = (C->functag == 3)
@@ -1012,7 +1013,7 @@ __global__ void force_finish_kernel(ForceParams<T> p, unsigned int* done) {
   double acc[3] = {0.0, 0.0, 0.0};
   for (int rec = threadIdx.x; rec < p.nwall; rec += blockDim.x)
     if (p.walls[rec].body == b)
-      for (int k = 0; k < 3; ++k) acc[k] += p.face_out[((int64_t)rec * p.ns + n) * 3 + k];
+      for (int k = 0; k < 3; ++k) acc[k] += p.face_out[((int64_t)n * p.nwall + rec) * 3 + k];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k = 0; k < 3; ++k) {
     double x = acc[k];
