@@ -83,20 +83,30 @@ struct Ar<double> {
   static __device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
 };
 
+// van Albada limiter in the form ((b^2+eps) a + (a^2+eps) b) / ((b^2+eps) +
+// (a^2+eps)): the two weights also make the denominator, and the weight of a
+// difference is shared by the two faces that limit with it
 template <typename T>
-__device__ __forceinline__ T van_albada(T a, T b, T eps) {
-  return Ar<T>::div((b * b + eps) * a + (a * a + eps) * b, a * a + b * b + T(2) * eps);
+__device__ __forceinline__ T va_weight(T a, T eps) { return a * a + eps; }
+template <typename T>
+__device__ __forceinline__ T van_albada_w(T a, T b, T wa, T wb) {
+  return Ar<T>::div(wb * a + wa * b, wa + wb);
 }
 
 // Roe flux through area vector (Sx, Sy) of a face moving with normal speed
 // vgn (grid velocity . unit normal).  W = (rho, u, v, p).  F = (mass, mx, my, E).
-// gg1 = gamma/(gamma-1), ig1 = 1/(gamma-1).
+// gg1 = gamma/(gamma-1); hef = 1/(2 efrac) for the entropy fix.
+// Written with the mass fluxes m = rho (q - vgn), the energy flux in the form
+// m H + p vgn (= E (q - vgn) + p q), and the wave sum factored as
+// D = s (1, u, v, H) + l2 a2 (1, u, v, k) + ct (w3 - w1) (0, nx, ny, q)
+//     + l2 rho~ (0, du, dv, u.du), s = w1 + w3 (the same sum as the textbook
+// form of the three waves).
 template <typename T>
 __device__ __forceinline__ void roe2d(const T* WL, const T* WR, T Sx, T Sy, T vgn, T gm1, T gg1,
-                                      T ig1, int efix, T efrac, T* F) {
+                                      int efix, T efrac, T hef, T* F) {
   const T A2 = Sx * Sx + Sy * Sy;
   const T iA = Ar<T>::rsq(A2);
-  const T A = A2 * iA;
+  const T hA = T(0.5) * (A2 * iA);
   const T nx = Sx * iA, ny = Sy * iA;
   const T irL = Ar<T>::rcp(WL[0]), irR = Ar<T>::rcp(WR[0]);
   const T qL = WL[1] * nx + WL[2] * ny;
@@ -120,30 +130,28 @@ __device__ __forceinline__ void roe2d(const T* WL, const T* WR, T Sx, T Sy, T vg
   const T qt = ut * nx + vt * ny;
   const T qtr = qt - vgn;
   T l1 = fabs(qtr - ct), l2 = fabs(qtr), l3 = fabs(qtr + ct);
-  if (efix) {
-    const T del = efrac * ct;
-    if (l1 < del) l1 = (l1 * l1 + del * del) * (T(0.5) * Ar<T>::rcp(del));
-    if (l3 < del) l3 = (l3 * l3 + del * del) * (T(0.5) * Ar<T>::rcp(del));
+  if (efix) {   // (l^2 + del^2) / (2 del) below del = efrac c~
+    const T del = efrac * ct, d2 = del * del, hid = hef * ict;
+    l1 = l1 < del ? (l1 * l1 + d2) * hid : l1;
+    l3 = l3 < del ? (l3 * l3 + d2) * hid : l3;
   }
   const T dp = WR[3] - WL[3], drho = WR[0] - WL[0], dq = qR - qL;
-  const T a1 = T(0.5) * (dp - rt * ct * dq) * ict2;
-  const T a3 = T(0.5) * (dp + rt * ct * dq) * ict2;
-  const T a2 = drho - dp * ict2;
+  const T m = rt * ct * dq, h = T(0.5) * ict2;
+  const T w1 = l1 * ((dp - m) * h), w3 = l3 * ((dp + m) * h);
+  const T l2a2 = l2 * (drho - dp * ict2), l2rt = l2 * rt;
   const T dux = (WR[1] - WL[1]) - dq * nx;
   const T duy = (WR[2] - WL[2]) - dq * ny;
-  const T udu = ut * dux + vt * duy;
-  const T w1 = l1 * a1, w3 = l3 * a3;
-  const T D0 = w1 + l2 * a2 + w3;
-  const T D1 = w1 * (ut - ct * nx) + l2 * (a2 * ut + rt * dux) + w3 * (ut + ct * nx);
-  const T D2 = w1 * (vt - ct * ny) + l2 * (a2 * vt + rt * duy) + w3 * (vt + ct * ny);
-  const T D3 = w1 * (Ht - ct * qt) + l2 * (a2 * kt + rt * udu) + w3 * (Ht + ct * qt);
-  const T qLr = qL - vgn, qRr = qR - vgn;
-  const T EL = WL[3] * ig1 + WL[0] * kL, ER = WR[3] * ig1 + WR[0] * kR;
-  const T hA = T(0.5) * A;
-  F[0] = hA * (WL[0] * qLr + WR[0] * qRr - D0);
-  F[1] = hA * (WL[0] * WL[1] * qLr + WL[3] * nx + WR[0] * WR[1] * qRr + WR[3] * nx - D1);
-  F[2] = hA * (WL[0] * WL[2] * qLr + WL[3] * ny + WR[0] * WR[2] * qRr + WR[3] * ny - D2);
-  F[3] = hA * (EL * qLr + WL[3] * qL + ER * qRr + WR[3] * qR - D3);
+  const T s13 = w1 + w3, dw = ct * (w3 - w1);
+  const T D0 = s13 + l2a2;
+  const T D1 = ut * D0 + nx * dw + l2rt * dux;
+  const T D2 = vt * D0 + ny * dw + l2rt * duy;
+  const T D3 = Ht * s13 + qt * dw + l2a2 * kt + l2rt * (ut * dux + vt * duy);
+  const T mL = WL[0] * (qL - vgn), mR = WR[0] * (qR - vgn);
+  const T ps = WL[3] + WR[3];
+  F[0] = hA * (mL + mR - D0);
+  F[1] = hA * (mL * WL[1] + mR * WR[1] + ps * nx - D1);
+  F[2] = hA * (mL * WL[2] + mR * WR[2] + ps * ny - D2);
+  F[3] = hA * (mL * HL + mR * HR + ps * vgn - D3);
 }
 
 // Viscous flux through (Sx, Sy) from cell gradients gL, gR = (ux,uy,vx,vy,Tx,Ty),
@@ -163,9 +171,10 @@ __device__ __forceinline__ void visc2d(const T* gL, const T* gR, T uL, T vL, T T
     g[2 * q] = bx + corr * ex;
     g[2 * q + 1] = by + corr * ey;
   }
-  const T div = g[0] + g[3];
-  const T txx = mu * (T(2) * g[0]) - T(2.0 / 3.0) * mu * div;
-  const T tyy = mu * (T(2) * g[3]) - T(2.0 / 3.0) * mu * div;
+  // mu (2 u_x - 2/3 div) = 4/3 mu u_x - 2/3 mu v_y, and alike
+  const T m43 = T(4.0 / 3.0) * mu, m23 = T(2.0 / 3.0) * mu;
+  const T txx = m43 * g[0] - m23 * g[3];
+  const T tyy = m43 * g[3] - m23 * g[0];
   const T txy = mu * (g[1] + g[2]);
   const T fx = txx * Sx + txy * Sy;
   const T fy = txy * Sx + tyy * Sy;
@@ -473,7 +482,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   const int ns = DYN ? C->ns : NS;
 
   const T gam = C->gamma, gm1 = C->gamma - T(1), eps = C->eps, efrac = C->ent_frac;
-  const T gg1 = gam / gm1, ig1 = T(1) / gm1;
+  const T gg1 = gam / gm1, hef = T(0.5) / efrac;
   const T mu = C->mu, kap = C->kappa, omega = C->omega;
   const int efix = C->entropy_fix;
   const bool moving = C->motion != 0;
@@ -613,15 +622,17 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const T a = W[q * NR + rL - st], bb = W[q * NR + rL], c = W[q * NR + rR], dd = W[q * NR + rR + st];
-      WL[q] = bb + T(0.5) * van_albada(bb - a, c - bb, eps);
-      WR[q] = c - T(0.5) * van_albada(c - bb, dd - c, eps);
+      const T d0 = bb - a, d1 = c - bb, d2 = dd - c;
+      const T w1 = va_weight(d1, eps);
+      WL[q] = bb + T(0.5) * van_albada_w(d0, d1, va_weight(d0, eps), w1);
+      WR[q] = c - T(0.5) * van_albada_w(d1, d2, w1, va_weight(d2, eps));
     }
     T sx, sy;
     rotv(f, sS[(2 * d) * NR + rR], sS[(2 * d + 1) * NR + rR], sx, sy);
     // normal grid velocity of the pitching face: thdot times its static factor
     const T vgn = moving ? f.thd * __ldg(P.g.q[G_VG + d] + gR) : T(0);
     T F[4];
-    roe2d(WL, WR, sx, sy, vgn, gm1, gg1, ig1, efix, efrac, F);
+    roe2d(WL, WR, sx, sy, vgn, gm1, gg1, efix, efrac, hef, F);
     if (VISC) {
       T gl[6], gr[6];
 #pragma unroll

@@ -17,12 +17,13 @@ namespace hbk {
 
 constexpr int T3I = 8, T3J = 8, T3K = 4;
 
+// Roe flux of the 3D path, written as roe2d with a third velocity component
 template <typename T>
 __device__ __forceinline__ void roe3d(const T* WL, const T* WR, T Sx, T Sy, T Sz, T vgn, T gm1, T gg1,
-                                      T ig1, int efix, T efrac, T* F) {
+                                      int efix, T efrac, T hef, T* F) {
   const T A2 = Sx * Sx + Sy * Sy + Sz * Sz;
   const T iA = Ar<T>::rsq(A2);
-  const T A = A2 * iA;
+  const T hA = T(0.5) * (A2 * iA);
   const T nx = Sx * iA, ny = Sy * iA, nz = Sz * iA;
   const T irL = Ar<T>::rcp(WL[0]), irR = Ar<T>::rcp(WR[0]);
   const T qL = WL[1] * nx + WL[2] * ny + WL[3] * nz;
@@ -48,32 +49,30 @@ __device__ __forceinline__ void roe3d(const T* WL, const T* WR, T Sx, T Sy, T Sz
   const T qtr = qt - vgn;
   T l1 = fabs(qtr - ct), l2 = fabs(qtr), l3 = fabs(qtr + ct);
   if (efix) {
-    const T del = efrac * ct;
-    if (l1 < del) l1 = (l1 * l1 + del * del) * (T(0.5) * Ar<T>::rcp(del));
-    if (l3 < del) l3 = (l3 * l3 + del * del) * (T(0.5) * Ar<T>::rcp(del));
+    const T del = efrac * ct, d2 = del * del, hid = hef * ict;
+    l1 = l1 < del ? (l1 * l1 + d2) * hid : l1;
+    l3 = l3 < del ? (l3 * l3 + d2) * hid : l3;
   }
   const T dp = WR[4] - WL[4], drho = WR[0] - WL[0], dq = qR - qL;
-  const T a1 = T(0.5) * (dp - rt * ct * dq) * ict2;
-  const T a3 = T(0.5) * (dp + rt * ct * dq) * ict2;
-  const T a2 = drho - dp * ict2;
+  const T m = rt * ct * dq, h = T(0.5) * ict2;
+  const T w1 = l1 * ((dp - m) * h), w3 = l3 * ((dp + m) * h);
+  const T l2a2 = l2 * (drho - dp * ict2), l2rt = l2 * rt;
   const T dux = (WR[1] - WL[1]) - dq * nx;
   const T duy = (WR[2] - WL[2]) - dq * ny;
   const T duz = (WR[3] - WL[3]) - dq * nz;
-  const T udu = ut * dux + vt * duy + wt * duz;
-  const T w1 = l1 * a1, w3 = l3 * a3;
-  const T D0 = w1 + l2 * a2 + w3;
-  const T D1 = w1 * (ut - ct * nx) + l2 * (a2 * ut + rt * dux) + w3 * (ut + ct * nx);
-  const T D2 = w1 * (vt - ct * ny) + l2 * (a2 * vt + rt * duy) + w3 * (vt + ct * ny);
-  const T D3 = w1 * (wt - ct * nz) + l2 * (a2 * wt + rt * duz) + w3 * (wt + ct * nz);
-  const T D4 = w1 * (Ht - ct * qt) + l2 * (a2 * kt + rt * udu) + w3 * (Ht + ct * qt);
-  const T qLr = qL - vgn, qRr = qR - vgn;
-  const T EL = WL[4] * ig1 + WL[0] * kL, ER = WR[4] * ig1 + WR[0] * kR;
-  const T hA = T(0.5) * A;
-  F[0] = hA * (WL[0] * qLr + WR[0] * qRr - D0);
-  F[1] = hA * (WL[0] * WL[1] * qLr + WL[4] * nx + WR[0] * WR[1] * qRr + WR[4] * nx - D1);
-  F[2] = hA * (WL[0] * WL[2] * qLr + WL[4] * ny + WR[0] * WR[2] * qRr + WR[4] * ny - D2);
-  F[3] = hA * (WL[0] * WL[3] * qLr + WL[4] * nz + WR[0] * WR[3] * qRr + WR[4] * nz - D3);
-  F[4] = hA * (EL * qLr + WL[4] * qL + ER * qRr + WR[4] * qR - D4);
+  const T s13 = w1 + w3, dw = ct * (w3 - w1);
+  const T D0 = s13 + l2a2;
+  const T D1 = ut * D0 + nx * dw + l2rt * dux;
+  const T D2 = vt * D0 + ny * dw + l2rt * duy;
+  const T D3 = wt * D0 + nz * dw + l2rt * duz;
+  const T D4 = Ht * s13 + qt * dw + l2a2 * kt + l2rt * (ut * dux + vt * duy + wt * duz);
+  const T mL = WL[0] * (qL - vgn), mR = WR[0] * (qR - vgn);
+  const T ps = WL[4] + WR[4];
+  F[0] = hA * (mL + mR - D0);
+  F[1] = hA * (mL * WL[1] + mR * WR[1] + ps * nx - D1);
+  F[2] = hA * (mL * WL[2] + mR * WR[2] + ps * ny - D2);
+  F[3] = hA * (mL * WL[3] + mR * WR[3] + ps * nz - D3);
+  F[4] = hA * (mL * HL + mR * HR + ps * vgn - D4);
 }
 
 // viscous flux through S from gradients gL, gR [4 quantities][3] (u, v, w, T),
@@ -147,7 +146,7 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
   T* sD = sAcc + NS * NV * NT;
 
   const T gam = C->gamma, gm1 = C->gamma - T(1), eps = C->eps, efrac = C->ent_frac;
-  const T gg1 = gam / gm1, ig1 = T(1) / gm1;
+  const T gg1 = gam / gm1, hef = T(0.5) / efrac;
   const T mu = C->mu, kap = C->kappa, omega = C->omega;
   const int efix = C->entropy_fix;
   const bool moving = C->motion != 0;
@@ -254,8 +253,10 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
         const T a = sW[q * NR + rL - st], b = sW[q * NR + rL], c = sW[q * NR + rR], dd = sW[q * NR + rR + st];
-        WL[q] = b + T(0.5) * van_albada(b - a, c - b, eps);
-        WR[q] = c - T(0.5) * van_albada(c - b, dd - c, eps);
+        const T d0 = b - a, d1 = c - b, d2 = dd - c;
+        const T w1 = va_weight(d1, eps);
+        WL[q] = b + T(0.5) * van_albada_w(d0, d1, va_weight(d0, eps), w1);
+        WR[q] = c - T(0.5) * van_albada_w(d1, d2, w1, va_weight(d2, eps));
       }
       const int64_t gR = pcell(Ri, Rj, Rk);
       T sx, sy;
@@ -269,7 +270,7 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
         vgn = (vgx * sx + vgy * sy) * Ar<T>::rsq(sx * sx + sy * sy + sz * sz);
       }
       T F[5];
-      roe3d(WL, WR, sx, sy, sz, vgn, gm1, gg1, ig1, efix, efrac, F);
+      roe3d(WL, WR, sx, sy, sz, vgn, gm1, gg1, efix, efrac, hef, F);
       if (VISC) {
         // ring index of L and R
         const int gRi = ((fk + 1) * GJ + (fj + 1)) * GI + (fi + 1);
