@@ -86,6 +86,31 @@ struct Ar<double> {
 // van Albada limiter in the form ((b^2+eps) a + (a^2+eps) b) / ((b^2+eps) +
 // (a^2+eps)): the two weights also make the denominator, and the weight of a
 // difference is shared by the two faces that limit with it
+// four (two) consecutive shared-memory values of a cell in one access
+__device__ __forceinline__ void lds4(const float* p, float& a, float& b, float& c, float& d) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = v.x; b = v.y; c = v.z; d = v.w;
+}
+__device__ __forceinline__ void lds4(const double* p, double& a, double& b, double& c, double& d) {
+  const double2 v = reinterpret_cast<const double2*>(p)[0], w = reinterpret_cast<const double2*>(p)[1];
+  a = v.x; b = v.y; c = w.x; d = w.y;
+}
+__device__ __forceinline__ void lds2(const float* p, float& a, float& b) {
+  const float2 v = *reinterpret_cast<const float2*>(p);
+  a = v.x; b = v.y;
+}
+__device__ __forceinline__ void lds2(const double* p, double& a, double& b) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  a = v.x; b = v.y;
+}
+__device__ __forceinline__ void sts4(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void sts4(double* p, double a, double b, double c, double d) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+  reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+}
+
 template <typename T>
 __device__ __forceinline__ T va_weight(T a, T eps) { return a * a + eps; }
 template <typename T>
@@ -470,7 +495,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   // PIPE: primitives and temperature double-buffered over snapshots, so
   // that the region of snapshot n+1 is staged while the faces of n run
   constexpr int NB = PIPE ? 2 : 1;
-  T* sW = sm;              // [NB][4][NR] primitives rho, u, v, p
+  T* sW = sm;              // [NB][NR][4] primitives (u, v, rho, p) of each cell
   T* sT = sW + NB * 4 * NR;   // [NB][NR] temperature gamma p / rho
   T* sIV = sT + NB * NR;   // [NR] 1 / volume
   T* sS = sIV + NR;        // [d*2+comp][NR] low-face vectors
@@ -514,7 +539,9 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   const int rown = (tj + 2) * RI + (ti + 2);
   const int64_t cown = (int64_t)(cj + 2) * P0 + (ci + 2);
 
-  // primitives of region cell r at snapshot n into buffer b
+  // primitives of region cell r at snapshot n into buffer b (the limiter
+  // acts on the Cartesian velocity components of the inertial frame, so the
+  // velocity is staged in that frame and the metrics are rotated instead)
   auto stage_cell = [&](int r, int n, int b) {
     const int ri = r % RI, rj = r / RI;
     const int i = i0 - 2 + ri, j = j0 - 2 + rj;
@@ -529,11 +556,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
       w3 = gm1 * (E - T(0.5) * rho * (w1 * w1 + w2 * w2));
       tt = gam * w3 * ir;
     }
-    T* W = sW + b * 4 * NR;
-    W[r] = w0;
-    W[NR + r] = w1;
-    W[2 * NR + r] = w2;
-    W[3 * NR + r] = w3;
+    sts4(sW + (b * NR + r) * 4, w1, w2, w0, w3);
     sT[b * NR + r] = tt;
   };
 
@@ -558,7 +581,9 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
     }
     const int gq = gj * GI + gi;
     const int r = (gj + 1) * RI + (gi + 1);
-    const T uc = W[NR + r], vc = W[2 * NR + r], Tc = TT[r];
+    T uc, vc;
+    lds2(W + 4 * r, uc, vc);
+    const T Tc = TT[r];
     T g[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     const int nb[4] = {r - 1, r + 1, r - RI, r + RI};
     const int fo[4] = {r, r + 1, r, r + RI};
@@ -571,7 +596,9 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
       sx *= sg;
       sy *= sg;
       const int o = nb[k];
-      const T du = W[NR + o] - uc, dv = W[2 * NR + o] - vc, dT = TT[o] - Tc;
+      T uo, vo;
+      lds2(W + 4 * o, uo, vo);
+      const T du = uo - uc, dv = vo - vc, dT = TT[o] - Tc;
       g[0] += du * sx; g[1] += du * sy;
       g[2] += dv * sx; g[3] += dv * sy;
       g[4] += dT * sx; g[5] += dT * sy;
@@ -618,10 +645,17 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
     const int rR = rL + st;
     // the face is the low face of cell R = (i0 + fi, j0 + fj) along d
     const int64_t gR = B.goff + (int64_t)(j0 + fj + 2) * P0 + (i0 + fi + 2);
-    T WL[4], WR[4];
+    // the four cells of the stencil, (u, v, rho, p) each
+    T Pa[4], Pb[4], Pc[4], Pd[4];
+    lds4(W + 4 * (rL - st), Pa[0], Pa[1], Pa[2], Pa[3]);
+    lds4(W + 4 * rL, Pb[0], Pb[1], Pb[2], Pb[3]);
+    lds4(W + 4 * rR, Pc[0], Pc[1], Pc[2], Pc[3]);
+    lds4(W + 4 * (rR + st), Pd[0], Pd[1], Pd[2], Pd[3]);
+    T WL[4], WR[4];   // (rho, u, v, p)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const T a = W[q * NR + rL - st], bb = W[q * NR + rL], c = W[q * NR + rR], dd = W[q * NR + rR + st];
+      const int k = q == 0 ? 2 : (q == 3 ? 3 : q - 1);
+      const T a = Pa[k], bb = Pb[k], c = Pc[k], dd = Pd[k];
       const T d0 = bb - a, d1 = c - bb, d2 = dd - c;
       const T w1 = va_weight(d1, eps);
       WL[q] = bb + T(0.5) * van_albada_w(d0, d1, va_weight(d0, eps), w1);
@@ -640,7 +674,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
       T tx, ty;
       rotv(f, __ldg(P.g.q[G_DC + 3 * d] + gR), __ldg(P.g.q[G_DC + 3 * d + 1] + gR), tx, ty);
       T Fv[4];
-      visc2d(gl, gr, W[NR + rL], W[2 * NR + rL], TT[rL], W[NR + rR], W[2 * NR + rR], TT[rR], tx, ty, sx,
+      visc2d(gl, gr, Pb[0], Pb[1], TT[rL], Pc[0], Pc[1], TT[rR], tx, ty, sx,
              sy, mu, kap, Fv);
 #pragma unroll
       for (int q = 0; q < 4; ++q) F[q] -= Fv[q];
@@ -680,24 +714,22 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
       T u0[NV];
 #pragma unroll
       for (int q = 0; q < NV; ++q) u0[q] = P.U0[base + q * B.plane];
-      const Fr<T> f = frame_at(C, n);
       const T rho = u0[0], irho = Ar<T>::rcp(rho);
       const T uv = u0[1] * irho, vv = u0[2] * irho;
       const T pp = gm1 * (u0[3] - T(0.5) * rho * (uv * uv + vv * vv));
       const T c2 = gam * pp * irho;
       const T cs = c2 * Ar<T>::rsq(c2);
+      // velocity relative to the pitching grid, in the static frame:
+      // R^T u - thdot z x (x_static - pivot)
       T urx = uv, ury = vv;
       if (moving) {
-        T xc, yc;
-        rotp(f, P.g.q[G_XC][B.goff + cown], P.g.q[G_XC + 1][B.goff + cown], xc, yc);
-        urx -= -f.thd * (yc - f.py);
-        ury -= f.thd * (xc - f.px);
+        const Fr<T> f = frame_at(C, n);
+        const T xc = P.g.q[G_XC][B.goff + cown], yc = P.g.q[G_XC + 1][B.goff + cown];
+        urx = f.c * uv + f.s * vv + f.thd * (yc - f.py);
+        ury = f.c * vv - f.s * uv - f.thd * (xc - f.px);
       }
-      T ax, ay, bx, by;
-      rotv(f, a0x, a0y, ax, ay);
-      rotv(f, b0x, b0y, bx, by);
       const T ma = ma2 * Ar<T>::rsq(ma2), mb = mb2 * Ar<T>::rsq(mb2);
-      T lam = fabs(urx * ax + ury * ay) + cs * ma + fabs(urx * bx + ury * by) + cs * mb;
+      T lam = fabs(urx * a0x + ury * a0y) + cs * ma + fabs(urx * b0x + ury * b0y) + cs * mb;
       if (VISC) {
         const T cv = (gam / C->prandtl > T(4.0 / 3.0)) ? gam / C->prandtl : T(4.0 / 3.0);
         lam += T(4) * cv * (mu * irho) * (ma2 + mb2) * iV;
