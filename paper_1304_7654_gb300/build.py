@@ -59,6 +59,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         cmd = [nvcc, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                "-I", CSRC, "-I", INCLUDE, "-c", src, "-o", obj]
+        if src.endswith("_f32.cu"):
+            # FP32 kernels flush subnormals: no quantity on the path comes near
+            # 1e-38, and the approximate reciprocal and reciprocal square root
+            # then need no range fix-up around the hardware instruction
+            cmd.insert(-4, "-ftz=true")
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

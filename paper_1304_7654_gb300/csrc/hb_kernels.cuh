@@ -86,15 +86,7 @@ struct Ar<double> {
 // van Albada limiter in the form ((b^2+eps) a + (a^2+eps) b) / ((b^2+eps) +
 // (a^2+eps)): the two weights also make the denominator, and the weight of a
 // difference is shared by the two faces that limit with it
-// four (two) consecutive shared-memory values of a cell in one access
-__device__ __forceinline__ void lds4(const float* p, float& a, float& b, float& c, float& d) {
-  const float4 v = *reinterpret_cast<const float4*>(p);
-  a = v.x; b = v.y; c = v.z; d = v.w;
-}
-__device__ __forceinline__ void lds4(const double* p, double& a, double& b, double& c, double& d) {
-  const double2 v = reinterpret_cast<const double2*>(p)[0], w = reinterpret_cast<const double2*>(p)[1];
-  a = v.x; b = v.y; c = w.x; d = w.y;
-}
+// two consecutive shared-memory values of a cell in one access; four in one store
 __device__ __forceinline__ void lds2(const float* p, float& a, float& b) {
   const float2 v = *reinterpret_cast<const float2*>(p);
   a = v.x; b = v.y;
@@ -109,6 +101,54 @@ __device__ __forceinline__ void sts4(float* p, float a, float b, float c, float 
 __device__ __forceinline__ void sts4(double* p, double a, double b, double c, double d) {
   reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
   reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+}
+
+// Two-lane arithmetic: on sm_100+ one packed FP32 instruction does both
+// lanes (the same rounding per lane as the scalar instruction); the FP64
+// form is the plain per-lane arithmetic.
+template <typename T>
+struct Two;
+template <>
+struct Two<float> {
+  using v = float2;
+  static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
+  static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+  static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+  static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+  static __device__ __forceinline__ float2 rcp(float2 a) {
+    return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y));
+  }
+  static __device__ __forceinline__ float2 ld(const float* p) { return *reinterpret_cast<const float2*>(p); }
+};
+template <>
+struct Two<double> {
+  using v = double2;
+  static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+  static __device__ __forceinline__ double2 add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+  static __device__ __forceinline__ double2 sub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+  static __device__ __forceinline__ double2 mul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+  static __device__ __forceinline__ double2 fma(double2 a, double2 b, double2 c) {
+    return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y));
+  }
+  static __device__ __forceinline__ double2 rcp(double2 a) { return make_double2(1.0 / a.x, 1.0 / a.y); }
+  static __device__ __forceinline__ double2 ld(const double* p) { return *reinterpret_cast<const double2*>(p); }
+};
+
+// MUSCL face states of two variables at once from the stencil a | b || c | d
+// (face between b and c): WL = b + va(b-a, c-b)/2, WR = c - va(c-b, d-c)/2
+template <typename T>
+__device__ __forceinline__ void muscl2(typename Two<T>::v a, typename Two<T>::v b, typename Two<T>::v c,
+                                       typename Two<T>::v d, T eps, typename Two<T>::v& wl,
+                                       typename Two<T>::v& wr) {
+  using M = Two<T>;
+  const auto e = M::make(eps, eps), h = M::make(T(0.5), T(0.5));
+  const auto d0 = M::sub(b, a), d1 = M::sub(c, b), d2 = M::sub(d, c);
+  const auto w0 = M::fma(d0, d0, e), w1 = M::fma(d1, d1, e), w2 = M::fma(d2, d2, e);
+  const auto sl = M::mul(M::fma(w1, d0, M::mul(w0, d1)), M::rcp(M::add(w0, w1)));
+  const auto sr = M::mul(M::fma(w2, d1, M::mul(w1, d2)), M::rcp(M::add(w1, w2)));
+  wl = M::fma(h, sl, b);
+  wr = M::sub(c, M::mul(h, sr));
 }
 
 template <typename T>
@@ -645,22 +685,18 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
     const int rR = rL + st;
     // the face is the low face of cell R = (i0 + fi, j0 + fj) along d
     const int64_t gR = B.goff + (int64_t)(j0 + fj + 2) * P0 + (i0 + fi + 2);
-    // the four cells of the stencil, (u, v, rho, p) each
-    T Pa[4], Pb[4], Pc[4], Pd[4];
-    lds4(W + 4 * (rL - st), Pa[0], Pa[1], Pa[2], Pa[3]);
-    lds4(W + 4 * rL, Pb[0], Pb[1], Pb[2], Pb[3]);
-    lds4(W + 4 * rR, Pc[0], Pc[1], Pc[2], Pc[3]);
-    lds4(W + 4 * (rR + st), Pd[0], Pd[1], Pd[2], Pd[3]);
-    T WL[4], WR[4];   // (rho, u, v, p)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int k = q == 0 ? 2 : (q == 3 ? 3 : q - 1);
-      const T a = Pa[k], bb = Pb[k], c = Pc[k], dd = Pd[k];
-      const T d0 = bb - a, d1 = c - bb, d2 = dd - c;
-      const T w1 = va_weight(d1, eps);
-      WL[q] = bb + T(0.5) * van_albada_w(d0, d1, va_weight(d0, eps), w1);
-      WR[q] = c - T(0.5) * van_albada_w(d1, d2, w1, va_weight(d2, eps));
-    }
+    // the four cells of the stencil, (u, v) and (rho, p) of each, limited
+    // two variables at a time
+    using M = Two<T>;
+    const T* Wa = W + 4 * (rL - st);
+    const T* Wb = W + 4 * rL;
+    const T* Wc = W + 4 * rR;
+    const T* Wd = W + 4 * (rR + st);
+    typename M::v uvL, uvR, rpL, rpR;
+    const typename M::v uvb = M::ld(Wb), uvc = M::ld(Wc);
+    muscl2<T>(M::ld(Wa), uvb, uvc, M::ld(Wd), eps, uvL, uvR);
+    muscl2<T>(M::ld(Wa + 2), M::ld(Wb + 2), M::ld(Wc + 2), M::ld(Wd + 2), eps, rpL, rpR);
+    const T WL[4] = {rpL.x, uvL.x, uvL.y, rpL.y}, WR[4] = {rpR.x, uvR.x, uvR.y, rpR.y};   // (rho, u, v, p)
     T sx, sy;
     rotv(f, sS[(2 * d) * NR + rR], sS[(2 * d + 1) * NR + rR], sx, sy);
     // normal grid velocity of the pitching face: thdot times its static factor
@@ -674,7 +710,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
       T tx, ty;
       rotv(f, __ldg(P.g.q[G_DC + 3 * d] + gR), __ldg(P.g.q[G_DC + 3 * d + 1] + gR), tx, ty);
       T Fv[4];
-      visc2d(gl, gr, Pb[0], Pb[1], TT[rL], Pc[0], Pc[1], TT[rR], tx, ty, sx,
+      visc2d(gl, gr, uvb.x, uvb.y, TT[rL], uvc.x, uvc.y, TT[rR], tx, ty, sx,
              sy, mu, kap, Fv);
 #pragma unroll
       for (int q = 0; q < 4; ++q) F[q] -= Fv[q];
