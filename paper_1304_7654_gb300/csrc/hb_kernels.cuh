@@ -67,7 +67,8 @@ __device__ __forceinline__ void rotp(const Fr<T>& f, T x, T y, T& ox, T& oy) {
 // Precision-specific arithmetic.  The FP32 path uses the hardware reciprocal
 // and reciprocal-square-root forms (a few ulp each, well inside the FP32
 // error budget of the residual); the FP64 path keeps correctly rounded
-// division and square root.
+// division and takes the 1-ulp reciprocal square root (one FP64 sequence
+// instead of a square root followed by a division).
 template <typename T>
 struct Ar;
 template <>
@@ -80,7 +81,7 @@ template <>
 struct Ar<double> {
   static __device__ __forceinline__ double div(double a, double b) { return a / b; }
   static __device__ __forceinline__ double rcp(double b) { return 1.0 / b; }
-  static __device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
+  static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 };
 
 // van Albada limiter in the form ((b^2+eps) a + (a^2+eps) b) / ((b^2+eps) +
@@ -94,6 +95,12 @@ __device__ __forceinline__ void lds2(const float* p, float& a, float& b) {
 __device__ __forceinline__ void lds2(const double* p, double& a, double& b) {
   const double2 v = *reinterpret_cast<const double2*>(p);
   a = v.x; b = v.y;
+}
+__device__ __forceinline__ void sts2(float* p, float a, float b) {
+  *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+__device__ __forceinline__ void sts2(double* p, double a, double b) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
 }
 __device__ __forceinline__ void sts4(float* p, float a, float b, float c, float d) {
   *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
@@ -229,8 +236,10 @@ __device__ __forceinline__ void visc2d(const T* gL, const T* gR, T uL, T vL, T T
   T g[6];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    const T bx = T(0.5) * (gL[2 * q] + gR[2 * q]);
-    const T by = T(0.5) * (gL[2 * q + 1] + gR[2 * q + 1]);
+    using M = Two<T>;
+    const auto bq = M::mul(M::make(T(0.5), T(0.5)),
+                           M::add(M::make(gL[2 * q], gL[2 * q + 1]), M::make(gR[2 * q], gR[2 * q + 1])));
+    const T bx = bq.x, by = bq.y;
     const T dphi = (q == 0) ? (uR - uL) : (q == 1) ? (vR - vL) : (TR - TL);
     const T corr = dphi * il - (bx * ex + by * ey);
     g[2 * q] = bx + corr * ex;
@@ -539,7 +548,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   T* sT = sW + NB * 4 * NR;   // [NB][NR] temperature gamma p / rho
   T* sIV = sT + NB * NR;   // [NR] 1 / volume
   T* sS = sIV + NR;        // [d*2+comp][NR] low-face vectors
-  T* sG = sS + 4 * NR;     // [6][NG] gradients on the 1-cell ring
+  T* sG = sS + 4 * NR;     // [3][NG][2] gradients (x, y) of u, v, T on the 1-cell ring
   T* sF = sG + 6 * NG;     // [NV][NF] face fluxes
   T* sAcc = sF + 4 * NF;   // [NS][NV][NT] flux balance per snapshot of each own cell
   T* sD = sAcc + NS * NV * NT;   // [NS][NS]
@@ -645,7 +654,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
     }
     const T iv = sIV[r];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) sG[q * NG + gq] = g[q] * iv;
+    for (int q = 0; q < 3; ++q) sts2(sG + 2 * (q * NG + gq), g[2 * q] * iv, g[2 * q + 1] * iv);
   };
 
   // one face of the tile from buffer b (faces no own cell uses are skipped)
@@ -706,7 +715,10 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
     if (VISC) {
       T gl[6], gr[6];
 #pragma unroll
-      for (int q = 0; q < 6; ++q) { gl[q] = sG[q * NG + gLi]; gr[q] = sG[q * NG + gRi]; }
+      for (int q = 0; q < 3; ++q) {
+        lds2(sG + 2 * (q * NG + gLi), gl[2 * q], gl[2 * q + 1]);
+        lds2(sG + 2 * (q * NG + gRi), gr[2 * q], gr[2 * q + 1]);
+      }
       T tx, ty;
       rotv(f, __ldg(P.g.q[G_DC + 3 * d] + gR), __ldg(P.g.q[G_DC + 3 * d + 1] + gR), tx, ty);
       T Fv[4];
