@@ -76,12 +76,23 @@ struct Ar<float> {
   static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
   static __device__ __forceinline__ float rcp(float b) { return __fdividef(1.0f, b); }
   static __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+  static __device__ __forceinline__ void rcp2(float a, float b, float& ia, float& ib) {
+    ia = __fdividef(1.0f, a);
+    ib = __fdividef(1.0f, b);
+  }
 };
 template <>
 struct Ar<double> {
   static __device__ __forceinline__ double div(double a, double b) { return a / b; }
   static __device__ __forceinline__ double rcp(double b) { return 1.0 / b; }
   static __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+  // 1/a and 1/b through one division, 1/(a b) (within 1.5 ulp); a, b are
+  // positive quantities of moderate range (densities, limiter weights)
+  static __device__ __forceinline__ void rcp2(double a, double b, double& ia, double& ib) {
+    const double r = 1.0 / (a * b);
+    ia = b * r;
+    ib = a * r;
+  }
 };
 
 // van Albada limiter in the form ((b^2+eps) a + (a^2+eps) b) / ((b^2+eps) +
@@ -138,7 +149,11 @@ struct Two<double> {
   static __device__ __forceinline__ double2 fma(double2 a, double2 b, double2 c) {
     return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y));
   }
-  static __device__ __forceinline__ double2 rcp(double2 a) { return make_double2(1.0 / a.x, 1.0 / a.y); }
+  static __device__ __forceinline__ double2 rcp(double2 a) {
+    double2 r;
+    Ar<double>::rcp2(a.x, a.y, r.x, r.y);
+    return r;
+  }
   static __device__ __forceinline__ double2 ld(const double* p) { return *reinterpret_cast<const double2*>(p); }
 };
 
@@ -180,7 +195,8 @@ __device__ __forceinline__ void roe2d(const T* WL, const T* WR, T Sx, T Sy, T vg
   const T iA = Ar<T>::rsq(A2);
   const T hA = T(0.5) * (A2 * iA);
   const T nx = Sx * iA, ny = Sy * iA;
-  const T irL = Ar<T>::rcp(WL[0]), irR = Ar<T>::rcp(WR[0]);
+  T irL, irR;
+  Ar<T>::rcp2(WL[0], WR[0], irL, irR);
   const T qL = WL[1] * nx + WL[2] * ny;
   const T qR = WR[1] * nx + WR[2] * ny;
   const T kL = T(0.5) * (WL[1] * WL[1] + WL[2] * WL[2]);

@@ -25,7 +25,8 @@ __device__ __forceinline__ void roe3d(const T* WL, const T* WR, T Sx, T Sy, T Sz
   const T iA = Ar<T>::rsq(A2);
   const T hA = T(0.5) * (A2 * iA);
   const T nx = Sx * iA, ny = Sy * iA, nz = Sz * iA;
-  const T irL = Ar<T>::rcp(WL[0]), irR = Ar<T>::rcp(WR[0]);
+  T irL, irR;
+  Ar<T>::rcp2(WL[0], WR[0], irL, irR);
   const T qL = WL[1] * nx + WL[2] * ny + WL[3] * nz;
   const T qR = WR[1] * nx + WR[2] * ny + WR[3] * nz;
   const T kL = T(0.5) * (WL[1] * WL[1] + WL[2] * WL[2] + WL[3] * WL[3]);
