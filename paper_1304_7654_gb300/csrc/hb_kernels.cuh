@@ -98,7 +98,15 @@ struct Ar<double> {
 // van Albada limiter in the form ((b^2+eps) a + (a^2+eps) b) / ((b^2+eps) +
 // (a^2+eps)): the two weights also make the denominator, and the weight of a
 // difference is shared by the two faces that limit with it
-// two consecutive shared-memory values of a cell in one access; four in one store
+// two or four consecutive shared-memory values of a cell in one access
+__device__ __forceinline__ void lds4(const float* p, float& a, float& b, float& c, float& d) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = v.x; b = v.y; c = v.z; d = v.w;
+}
+__device__ __forceinline__ void lds4(const double* p, double& a, double& b, double& c, double& d) {
+  const double2 v = reinterpret_cast<const double2*>(p)[0], w = reinterpret_cast<const double2*>(p)[1];
+  a = v.x; b = v.y; c = w.x; d = w.y;
+}
 __device__ __forceinline__ void lds2(const float* p, float& a, float& b) {
   const float2 v = *reinterpret_cast<const float2*>(p);
   a = v.x; b = v.y;

@@ -138,9 +138,9 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
   const int n0 = B.n[0], n1 = B.n[1], n2 = B.n[2];
   const int64_t sJ = P0, sK = (int64_t)P0 * P1;
 
-  T* sW = sm;              // [5][NR] rho, u, v, w, p
-  T* sT = sW + 5 * NR;     // [NR]
-  T* sIV = sT + NR;        // [NR]
+  T* sW = sm;              // [NR][4] (u, v, w, p) of each cell
+  T* sRT = sW + 4 * NR;    // [NR][2] (rho, T = gamma p / rho)
+  T* sIV = sRT + 2 * NR;   // [NR]
   T* sG = sIV + NR;        // [12][NG]
   T* sF = sG + 12 * NG;    // [NV][NF]
   T* sAcc = sF + NV * NF;  // [NS][NV][NT]
@@ -192,9 +192,8 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
         w[4] = gm1 * (u[4 * B.plane] - T(0.5) * rho * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]));
         tt = gam * w[4] * ir;
       }
-#pragma unroll
-      for (int q = 0; q < 5; ++q) sW[q * NR + r] = w[q];
-      sT[r] = tt;
+      sts4(sW + 4 * r, w[1], w[2], w[3], w[4]);
+      sts2(sRT + 2 * r, w[0], tt);
     }
     __syncthreads();
     if (VISC) {
@@ -212,7 +211,9 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
           for (int q = 0; q < 12; ++q) sG[q * NG + gq] = T(0);
           continue;
         }
-        const T pc[4] = {sW[NR + r], sW[2 * NR + r], sW[3 * NR + r], sT[r]};
+        T pc[4], pdum;
+        lds4(sW + 4 * r, pc[0], pc[1], pc[2], pdum);
+        pc[3] = sRT[2 * r + 1];
         const int rs[3] = {1, RI, RI * RJ};
         const int64_t cs[3] = {1, sJ, sK};
         const int64_t c = pcell(i, j, k);
@@ -227,7 +228,9 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
             rotv(f, s0, s1, sx, sy);
             const T sg = side ? T(0.5) : T(-0.5);
             const T sv[3] = {sg * sx, sg * sy, sg * s2};
-            const T dphi[4] = {sW[NR + o] - pc[0], sW[2 * NR + o] - pc[1], sW[3 * NR + o] - pc[2], sT[o] - pc[3]};
+            T po[4];
+            lds4(sW + 4 * o, po[0], po[1], po[2], po[3]);
+            const T dphi[4] = {po[0] - pc[0], po[1] - pc[1], po[2] - pc[2], sRT[2 * o + 1] - pc[3]};
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -250,15 +253,25 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
       const int st = (d == 0) ? 1 : (d == 1 ? RI : RI * RJ);
       const int rR = rcell(fi + 2, fj + 2, fk + 2);
       const int rL = rR - st;
-      T WL[5], WR[5];
-#pragma unroll
-      for (int q = 0; q < 5; ++q) {
-        const T a = sW[q * NR + rL - st], b = sW[q * NR + rL], c = sW[q * NR + rR], dd = sW[q * NR + rR + st];
+      // (u, v) and (w, p) limited two at a time, rho alone
+      using M = Two<T>;
+      const T* Wa = sW + 4 * (rL - st);
+      const T* Wb = sW + 4 * rL;
+      const T* Wc = sW + 4 * rR;
+      const T* Wd = sW + 4 * (rR + st);
+      typename M::v uvL, uvR, wpL, wpR;
+      const typename M::v uvb = M::ld(Wb), uvc = M::ld(Wc), wpb = M::ld(Wb + 2), wpc = M::ld(Wc + 2);
+      muscl2<T>(M::ld(Wa), uvb, uvc, M::ld(Wd), eps, uvL, uvR);
+      muscl2<T>(M::ld(Wa + 2), wpb, wpc, M::ld(Wd + 2), eps, wpL, wpR);
+      T rhoL, rhoR;
+      {
+        const T a = sRT[2 * (rL - st)], b = sRT[2 * rL], c = sRT[2 * rR], dd = sRT[2 * (rR + st)];
         const T d0 = b - a, d1 = c - b, d2 = dd - c;
         const T w1 = va_weight(d1, eps);
-        WL[q] = b + T(0.5) * van_albada_w(d0, d1, va_weight(d0, eps), w1);
-        WR[q] = c - T(0.5) * van_albada_w(d1, d2, w1, va_weight(d2, eps));
+        rhoL = b + T(0.5) * van_albada_w(d0, d1, va_weight(d0, eps), w1);
+        rhoR = c - T(0.5) * van_albada_w(d1, d2, w1, va_weight(d2, eps));
       }
+      const T WL[5] = {rhoL, uvL.x, uvL.y, wpL.x, wpL.y}, WR[5] = {rhoR, uvR.x, uvR.y, wpR.x, wpR.y};
       const int64_t gR = pcell(Ri, Rj, Rk);
       T sx, sy;
       rotv(f, __ldg(gS[d][0] + gR), __ldg(gS[d][1] + gR), sx, sy);
@@ -283,8 +296,8 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
         T tx, ty;
         rotv(f, __ldg(gDc[d][0] + gR), __ldg(gDc[d][1] + gR), tx, ty);
         const T tz = __ldg(gDc[d][2] + gR);
-        const T pL[4] = {sW[NR + rL], sW[2 * NR + rL], sW[3 * NR + rL], sT[rL]};
-        const T pR[4] = {sW[NR + rR], sW[2 * NR + rR], sW[3 * NR + rR], sT[rR]};
+        const T pL[4] = {uvb.x, uvb.y, wpb.x, sRT[2 * rL + 1]};
+        const T pR[4] = {uvc.x, uvc.y, wpc.x, sRT[2 * rR + 1]};
         T Fv[5];
         visc3d(gl, gr, pL, pR, tx, ty, tz, sx, sy, sz, mu, kap, Fv);
 #pragma unroll
