@@ -657,28 +657,37 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
     T uc, vc;
     lds2(W + 4 * r, uc, vc);
     const T Tc = TT[r];
+    // summed with the static face vectors (the low face enters with -S,
+    // the high one with +S) and rotated once per quantity into the frame
+    // of snapshot n: the sum is linear in S
     T g[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     const int nb[4] = {r - 1, r + 1, r - RI, r + RI};
     const int fo[4] = {r, r + 1, r, r + RI};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int d = k >> 1;
-      const T sg = (k & 1) ? T(0.5) : T(-0.5);
-      T sx, sy;
-      rotv(f, sS[(2 * d) * NR + fo[k]], sS[(2 * d + 1) * NR + fo[k]], sx, sy);
-      sx *= sg;
-      sy *= sg;
+      const T sx = sS[(2 * d) * NR + fo[k]], sy = sS[(2 * d + 1) * NR + fo[k]];
       const int o = nb[k];
       T uo, vo;
       lds2(W + 4 * o, uo, vo);
       const T du = uo - uc, dv = vo - vc, dT = TT[o] - Tc;
-      g[0] += du * sx; g[1] += du * sy;
-      g[2] += dv * sx; g[3] += dv * sy;
-      g[4] += dT * sx; g[5] += dT * sy;
+      if (k & 1) {
+        g[0] += du * sx; g[1] += du * sy;
+        g[2] += dv * sx; g[3] += dv * sy;
+        g[4] += dT * sx; g[5] += dT * sy;
+      } else {
+        g[0] -= du * sx; g[1] -= du * sy;
+        g[2] -= dv * sx; g[3] -= dv * sy;
+        g[4] -= dT * sx; g[5] -= dT * sy;
+      }
     }
-    const T iv = sIV[r];
+    const T hiv = T(0.5) * sIV[r];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) sts2(sG + 2 * (q * NG + gq), g[2 * q] * iv, g[2 * q + 1] * iv);
+    for (int q = 0; q < 3; ++q) {
+      T gx = g[2 * q], gy = g[2 * q + 1];
+      if (moving) rotv(f, g[2 * q], g[2 * q + 1], gx, gy);
+      sts2(sG + 2 * (q * NG + gq), gx * hiv, gy * hiv);
+    }
   };
 
   // one face of the tile from buffer b (faces no own cell uses are skipped)
