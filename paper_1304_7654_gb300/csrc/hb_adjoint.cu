@@ -36,23 +36,25 @@ __device__ __forceinline__ T sgnf(T x) { return x < 0.0 ? -1.0 : 1.0; }
 
 // primitives (rho, u, v, p) and T from conservative U
 __device__ __forceinline__ void prim4(const T* U, T gm1, T gam, T* W, T& Tt) {
+  const T ir = 1.0 / U[0];
   W[0] = U[0];
-  W[1] = U[1] / U[0];
-  W[2] = U[2] / U[0];
+  W[1] = U[1] * ir;
+  W[2] = U[2] * ir;
   W[3] = gm1 * (U[3] - 0.5 * U[0] * (W[1] * W[1] + W[2] * W[2]));
-  Tt = gam * W[3] / W[0];
+  Tt = gam * W[3] * ir;
 }
 
 // Wbar (rho, u, v, p) and Tbar -> Ubar
 __device__ __forceinline__ void prim4_adj(const T* W, T Tbar, const T* Wb_in, T gm1, T gam, T* Ub) {
   T Wb[4] = {Wb_in[0], Wb_in[1], Wb_in[2], Wb_in[3]};
+  const T rho = W[0], u = W[1], v = W[2], ir = 1.0 / rho;
   // T = gam p / rho
-  Wb[3] += Tbar * gam / W[0];
-  Wb[0] -= Tbar * gam * W[3] / (W[0] * W[0]);
-  const T rho = W[0], u = W[1], v = W[2];
-  Ub[0] = Wb[0] - Wb[1] * u / rho - Wb[2] * v / rho + Wb[3] * gm1 * 0.5 * (u * u + v * v);
-  Ub[1] = Wb[1] / rho - Wb[3] * gm1 * u;
-  Ub[2] = Wb[2] / rho - Wb[3] * gm1 * v;
+  const T tg = Tbar * gam * ir;
+  Wb[3] += tg;
+  Wb[0] -= tg * W[3] * ir;
+  Ub[0] = Wb[0] - (Wb[1] * u + Wb[2] * v) * ir + Wb[3] * gm1 * 0.5 * (u * u + v * v);
+  Ub[1] = Wb[1] * ir - Wb[3] * gm1 * u;
+  Ub[2] = Wb[2] * ir - Wb[3] * gm1 * v;
   Ub[3] = Wb[3] * gm1;
 }
 
@@ -65,49 +67,55 @@ __device__ __forceinline__ void cons4_adj(const T* W, const T* Ub, T ig1, T* Wb)
   Wb[3] = Ub[3] * ig1;
 }
 
-// van Albada va(a, b) = N / Dn and its partial derivatives
-__device__ __forceinline__ void va_d(T a, T b, T eps, T& da, T& db) {
+// van Albada va(a, b) = N / Dn, returned, and its partial derivatives
+__device__ __forceinline__ T va_d(T a, T b, T eps, T& da, T& db) {
   const T N = (b * b + eps) * a + (a * a + eps) * b;
-  const T Dn = a * a + b * b + 2.0 * eps;
-  const T v = N / Dn;
-  da = (b * b + eps + 2.0 * a * b - v * 2.0 * a) / Dn;
-  db = (2.0 * a * b + a * a + eps - v * 2.0 * b) / Dn;
+  const T iD = 1.0 / (a * a + b * b + 2.0 * eps);
+  const T v = N * iD;
+  da = (b * b + eps + 2.0 * a * b - v * 2.0 * a) * iD;
+  db = (2.0 * a * b + a * a + eps - v * 2.0 * b) * iD;
+  return v;
 }
 
 // Reverse of roe2d (plain FP64 forms): Fb -> WLb, WRb (accumulated)
 __device__ void roe2d_adj(const T* WL, const T* WR, T Sx, T Sy, T vgn, T gam, int efix, T efrac,
                           const T* Fb, T* WLb, T* WRb) {
   const T gm1 = gam - 1.0, gg1 = gam / gm1, ig1 = 1.0 / gm1;
-  const T A = sqrt(Sx * Sx + Sy * Sy);
-  const T nx = Sx / A, ny = Sy / A;
+  // each quotient below multiplies by one reciprocal taken once
+  const T A = sqrt(Sx * Sx + Sy * Sy), iA = 1.0 / A;
+  const T nx = Sx * iA, ny = Sy * iA;
   // ---- forward
   const T rL = WL[0], uL = WL[1], vL = WL[2], pL = WL[3];
   const T rR = WR[0], uR = WR[1], vR = WR[2], pR = WR[3];
+  const T irL = 1.0 / rL, irR = 1.0 / rR;
   const T qL = uL * nx + vL * ny, qR = uR * nx + vR * ny;
   const T kL = 0.5 * (uL * uL + vL * vL), kR = 0.5 * (uR * uR + vR * vR);
-  const T HL = gg1 * pL / rL + kL, HR = gg1 * pR / rR + kR;
-  const T rr = rR / rL;
+  const T HL = gg1 * pL * irL + kL, HR = gg1 * pR * irR + kR;
+  const T rr = rR * irL;
   const T r = sqrt(rr);
+  const T ir = r * rL * irR;   // 1 / r = r / rr
   const T rt = r * rL;
-  const T den = 1.0 + r;
-  const T ut = (uL + r * uR) / den, vt = (vL + r * vR) / den, Ht = (HL + r * HR) / den;
+  const T den = 1.0 + r, iden = 1.0 / den;
+  const T ut = (uL + r * uR) * iden, vt = (vL + r * vR) * iden, Ht = (HL + r * HR) * iden;
   const T kt = 0.5 * (ut * ut + vt * vt);
   const T ct2 = gm1 * (Ht - kt);
-  const T ct = sqrt(ct2);
+  const T ct = sqrt(ct2), ict2 = 1.0 / ct2, ict = ct * ict2;
   const T qt = ut * nx + vt * ny;
   const T qtr = qt - vgn;
   const T x1 = qtr - ct, x3 = qtr + ct;
   T l1 = fabs(x1), l2 = fabs(qtr), l3 = fabs(x3);
   const T del = efrac * ct;
+  const T idel = efix ? 1.0 / del : 0.0;
   bool f1 = false, f3 = false;
   if (efix) {
-    if (l1 < del) { l1 = (l1 * l1 + del * del) / (2.0 * del); f1 = true; }
-    if (l3 < del) { l3 = (l3 * l3 + del * del) / (2.0 * del); f3 = true; }
+    if (l1 < del) { l1 = (l1 * l1 + del * del) * (0.5 * idel); f1 = true; }
+    if (l3 < del) { l3 = (l3 * l3 + del * del) * (0.5 * idel); f3 = true; }
   }
   const T dp = pR - pL, drho = rR - rL, dq = qR - qL;
-  const T a1 = (dp - rt * ct * dq) / (2.0 * ct2);
-  const T a3 = (dp + rt * ct * dq) / (2.0 * ct2);
-  const T a2 = drho - dp / ct2;
+  const T h2 = 0.5 * ict2;   // 1 / (2 ct2)
+  const T a1 = (dp - rt * ct * dq) * h2;
+  const T a3 = (dp + rt * ct * dq) * h2;
+  const T a2 = drho - dp * ict2;
   const T dux = (uR - uL) - dq * nx, duy = (vR - vL) - dq * ny;
   const T udu = ut * dux + vt * duy;
   const T w1 = l1 * a1, w3 = l3 * a3;
@@ -185,27 +193,27 @@ __device__ void roe2d_adj(const T* WL, const T* WR, T Sx, T Sy, T vgn, T gam, in
   uRb += duxb; uLb -= duxb; dqb -= duxb * nx;
   vRb += duyb; vLb -= duyb; dqb -= duyb * ny;
   // a2 = drho - dp / ct2
-  drhob += a2b; dpb -= a2b / ct2; ct2b += a2b * dp / (ct2 * ct2);
+  drhob += a2b; dpb -= a2b * ict2; ct2b += a2b * dp * ict2 * ict2;
   // a3 = (dp + rt ct dq) / (2 ct2)
-  dpb += a3b / (2.0 * ct2); rtb += a3b * ct * dq / (2.0 * ct2); ctb += a3b * rt * dq / (2.0 * ct2);
-  dqb += a3b * rt * ct / (2.0 * ct2); ct2b -= a3b * a3 / ct2;
+  dpb += a3b * h2; rtb += a3b * ct * dq * h2; ctb += a3b * rt * dq * h2;
+  dqb += a3b * rt * ct * h2; ct2b -= a3b * a3 * ict2;
   // a1 = (dp - rt ct dq) / (2 ct2)
-  dpb += a1b / (2.0 * ct2); rtb -= a1b * ct * dq / (2.0 * ct2); ctb -= a1b * rt * dq / (2.0 * ct2);
-  dqb -= a1b * rt * ct / (2.0 * ct2); ct2b -= a1b * a1 / ct2;
+  dpb += a1b * h2; rtb -= a1b * ct * dq * h2; ctb -= a1b * rt * dq * h2;
+  dqb -= a1b * rt * ct * h2; ct2b -= a1b * a1 * ict2;
   pRb += dpb; pLb -= dpb; rRb += drhob; rLb -= drhob; qRb += dqb; qLb -= dqb;
   // wave speeds
   T qtrb = 0, delb = 0;
   {
     const T ax = fabs(x1);
     T x1b;
-    if (f1) { x1b = l1b * (ax / del) * sgnf(x1); delb += l1b * (0.5 - ax * ax / (2.0 * del * del)); }
+    if (f1) { x1b = l1b * (ax * idel) * sgnf(x1); delb += l1b * (0.5 - 0.5 * ax * ax * idel * idel); }
     else x1b = l1b * sgnf(x1);
     qtrb += x1b; ctb -= x1b;
   }
   {
     const T ax = fabs(x3);
     T x3b;
-    if (f3) { x3b = l3b * (ax / del) * sgnf(x3); delb += l3b * (0.5 - ax * ax / (2.0 * del * del)); }
+    if (f3) { x3b = l3b * (ax * idel) * sgnf(x3); delb += l3b * (0.5 - 0.5 * ax * ax * idel * idel); }
     else x3b = l3b * sgnf(x3);
     qtrb += x3b; ctb += x3b;
   }
@@ -213,21 +221,21 @@ __device__ void roe2d_adj(const T* WL, const T* WR, T Sx, T Sy, T vgn, T gam, in
   ctb += delb * efrac;
   qtb += qtrb;
   utb += qtb * nx; vtb += qtb * ny;
-  ct2b += ctb / (2.0 * ct);
+  ct2b += ctb * (0.5 * ict);
   Htb += gm1 * ct2b; ktb -= gm1 * ct2b;
   utb += ktb * ut; vtb += ktb * vt;
   // Roe averages
   T HLb = 0, HRb = 0, rb = 0, denb = 0;
-  HLb += Htb / den; HRb += Htb * r / den; rb += Htb * HR / den; denb -= Htb * Ht / den;
-  uLb += utb / den; uRb += utb * r / den; rb += utb * uR / den; denb -= utb * ut / den;
-  vLb += vtb / den; vRb += vtb * r / den; rb += vtb * vR / den; denb -= vtb * vt / den;
+  HLb += Htb * iden; HRb += Htb * r * iden; rb += Htb * HR * iden; denb -= Htb * Ht * iden;
+  uLb += utb * iden; uRb += utb * r * iden; rb += utb * uR * iden; denb -= utb * ut * iden;
+  vLb += vtb * iden; vRb += vtb * r * iden; rb += vtb * vR * iden; denb -= vtb * vt * iden;
   rb += denb;
   rb += rtb * rL; rLb += rtb * r;
-  const T rrb = rb / (2.0 * r);
-  rRb += rrb / rL; rLb -= rrb * rr / rL;
+  const T rrb = rb * (0.5 * ir);
+  rRb += rrb * irL; rLb -= rrb * rr * irL;
   // H = gg1 p / rho + k
-  pLb += HLb * gg1 / rL; rLb -= HLb * gg1 * pL / (rL * rL); kLb += HLb;
-  pRb += HRb * gg1 / rR; rRb -= HRb * gg1 * pR / (rR * rR); kRb += HRb;
+  pLb += HLb * gg1 * irL; rLb -= HLb * gg1 * pL * irL * irL; kLb += HLb;
+  pRb += HRb * gg1 * irR; rRb -= HRb * gg1 * pR * irR * irR; kRb += HRb;
   uLb += kLb * uL; vLb += kLb * vL; uRb += kRb * uR; vRb += kRb * vR;
   uLb += qLb * nx; vLb += qLb * ny; uRb += qRb * nx; vRb += qRb * ny;
   WLb[0] += rLb; WLb[1] += uLb; WLb[2] += vLb; WLb[3] += pLb;
@@ -411,14 +419,8 @@ __global__ void adj_faces_kernel(AdjParams p) {
     T dL[4][2], dR[4][2];
     for (int q = 0; q < 4; ++q) {
       const T a = W[1][q] - W[0][q], bq = W[2][q] - W[1][q], cq = W[3][q] - W[2][q];
-      const T N1 = (bq * bq + C->eps) * a + (a * a + C->eps) * bq;
-      const T D1 = a * a + bq * bq + 2.0 * C->eps;
-      const T N2 = (cq * cq + C->eps) * bq + (bq * bq + C->eps) * cq;
-      const T D2 = bq * bq + cq * cq + 2.0 * C->eps;
-      WL[q] = W[1][q] + 0.5 * (N1 / D1);
-      WR[q] = W[2][q] - 0.5 * (N2 / D2);
-      va_d(a, bq, C->eps, dL[q][0], dL[q][1]);
-      va_d(bq, cq, C->eps, dR[q][0], dR[q][1]);
+      WL[q] = W[1][q] + 0.5 * va_d(a, bq, C->eps, dL[q][0], dL[q][1]);
+      WR[q] = W[2][q] - 0.5 * va_d(bq, cq, C->eps, dR[q][0], dR[q][1]);
     }
     T WLb[4] = {0, 0, 0, 0}, WRb[4] = {0, 0, 0, 0};
     roe2d_adj(WL, WR, sx, sy, vgn, gam, C->entropy_fix, C->ent_frac, Fb, WLb, WRb);
@@ -471,11 +473,8 @@ __global__ void adj_faces_kernel(AdjParams p) {
   }
   double* out = p.buf + (face * p.ns + n) * 32;
   for (int k = 0; k < 8; ++k) {
-    T u[4];
-    for (int v = 0; v < NV; ++v) u[v] = Ub[v * B.plane + sc[k]];
-    T Wk[4], Tk, Ubk[4];
-    prim4(u, gm1, gam, Wk, Tk);
-    prim4_adj(Wk, Tb[k], Wb[k], gm1, gam, Ubk);
+    T Ubk[4];
+    prim4_adj(W[k], Tb[k], Wb[k], gm1, gam, Ubk);
     for (int v = 0; v < NV; ++v) out[k * 4 + v] = Ubk[v];
   }
 }
