@@ -189,7 +189,7 @@ hb_status hb_residual(hb_ctx* ctx, const void* U, void* R, void* stream);
  * (all cases, all phases, bounded-spin grid barriers: a barrier that waits
  * longer than HB_BARRIER_TIMEOUT_MS, default 2000, latches HB_ERR_TIMEOUT
  * and the launch returns); chunks are captured and replayed as CUDA graphs
- * where the driver allows it. */
+ * where stream capture is available. */
 hb_status hb_rk_smooth(hb_ctx* ctx, void* U, int n_iter, double* norms_dev, void* stream);
 
 /* Force coefficients of every body at every snapshot, packed
