@@ -605,6 +605,34 @@ def _traffic_record(name):
     return rec["dram_bytes_per_launch"] if rec else None
 
 
+def run_profile_adjoint(args):
+    """ncu entry point for the adjoint: warmup + steps pairs of an FP64
+    residual and an adjoint residual on the 4-block 512x256 laminar N_H=4
+    case, nothing timed."""
+    import torch
+    from paper_1304_7654_gb300 import cases as C
+    from paper_1304_7654_gb300 import hb
+    if args.profile != "fp64":
+        raise SystemExit("the adjoint is FP64: use --profile fp64")
+    cs = C.adjoint_ogrid4()
+    cs.alpha0_deg = 2.0
+    ctx = hb.HBContext(cs, "fp64")
+    U = ctx.new_state()
+    ctx.init_state(U, torch.as_tensor(C.noise(cs), device="cuda"), 0.01)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    psi = torch.randn(ctx.size, dtype=torch.float64, device="cuda", generator=g)
+    R, r = ctx.new_state(), ctx.new_state()
+    for _ in range(args.warmup + args.steps):
+        ctx.residual(U, R)
+        ctx.adjoint_residual(U, psi, 0.5, r)
+    torch.cuda.synchronize()
+    st = ctx.sync_status()
+    print(json.dumps({"profile": "fp64 adjoint", "iterations": args.warmup + args.steps, "status": st,
+                      "r_adj_norm": float(r.norm())}))
+    return 0 if st == 0 else 1
+
+
 def run_profile(args):
     """Small entry point for ncu captures: warmup + steps RK iterations (and
     force reductions) of the workload in one precision, nothing timed."""
@@ -613,6 +641,8 @@ def run_profile(args):
     hbuild.build()
     from paper_1304_7654_gb300 import cases as C
     from paper_1304_7654_gb300 import hb
+    if args.profile_shape == "adjoint":
+        return run_profile_adjoint(args)
     if args.profile_shape:
         cs = {"tc1": C.paper_tc1, "tc2": C.paper_tc2, "box3d": C.box3d}[args.profile_shape]()
         ctx = hb.HBContext(cs, args.profile)
@@ -659,8 +689,9 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--profile", choices=["fp32", "fp64"], default=None)
     ap.add_argument("--profile-batch", action="store_true")
-    ap.add_argument("--profile-shape", default=None, choices=["tc1", "tc2", "box3d"],
-                    help="with --profile: a paper-shaped workload or the 3D box instead of the 8-block O-grid")
+    ap.add_argument("--profile-shape", default=None, choices=["tc1", "tc2", "box3d", "adjoint"],
+                    help="with --profile: a paper-shaped workload, the 3D box or (fp64) the adjoint "
+                         "case instead of the 8-block O-grid")
     ap.add_argument("--tuning", default=None,
                     help="mode,TI,TJ (0 per-phase, 1 persistent; +2 separate halo passes instead of the fused ghost fill)")
     args = ap.parse_args()
