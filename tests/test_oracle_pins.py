@@ -565,3 +565,58 @@ def test_td_residual_at_rest_in_time_is_the_steady_residual():
     Rt = o.td_residual(U, U, U, 0.0, 0.1)
     # (3/2 - 2 + 1/2) U is zero up to the rounding of the BDF combination
     assert np.abs(o.unpack(Rt) - o.unpack(R0)).max() <= 1e-12 * np.abs(o.unpack(R0)).max()
+
+
+# ------------------------------------- viscous flux, linear velocity field --
+def _affine_channel(ni, nj, viscous):
+    """Single-block channel on a skewed affine grid (every cell the same
+    parallelogram), steady (N_H = 0)."""
+    xi = np.linspace(0.0, 2.0, ni + 1)
+    eta = np.linspace(0.0, 1.0, nj + 1)
+    X, Y = np.meshgrid(xi, eta)
+    gn = np.stack([X + 0.3 * Y, 0.1 * X + Y], axis=-1)
+    ext = C.extend_ghost_nodes(gn, 2, (False, False))
+    side_bc = {(0, 0): (C.BC_FARFIELD, -1), (0, 1): (C.BC_FARFIELD, -1),
+               (1, 0): (C.BC_SLIP, -1), (1, 1): (C.BC_SLIP, -1)}
+    bl, cuts, bcs = C.split_blocks(ext, 2, (ni, nj), (False, False), side_bc,
+                                   [C.BlockSpec((0, 0), (ni, nj))])
+    return C.Case(name="affine_channel", dim=2, n_harm=0, mach=0.5, omega=0.1, viscous=viscous,
+                  blocks=bl, cuts=cuts, bcs=bcs, n_bodies=0, seed=1)
+
+
+def test_viscous_flux_of_a_linear_velocity_field_is_exact_on_an_affine_grid():
+    """Reading A6 (Green-Gauss cell gradients from face means, face gradient =
+    mean + edge-normal correction, Stokes stress, Fourier heat flux) with the
+    constant viscosity of A17.  For uniform density and pressure and a linear
+    velocity u = u0 + A x on a grid of equal parallelograms, every gradient is
+    exact, the stress tau = mu (A + A^T - 2/3 tr(A) I) is constant and T is
+    uniform, so the viscous part of each interior residual (viscous run minus
+    inviscid run) is, by the divergence theorem, zero in mass and momentum
+    and -V tau : A in energy.  A wrong gradient factor, stress coefficient or
+    sign, or a dropped -2/3 div term, breaks it."""
+    ni, nj = 24, 16
+    A = np.array([[0.03, -0.02], [0.05, 0.01]])          # A[i][j] = d u_i / d x_j
+    u0 = np.array([0.5, 0.0])
+    on, off = Oracle(_affine_channel(ni, nj, True)), Oracle(_affine_channel(ni, nj, False))
+    vol, xc, _ = on.geometry(0)
+    U = np.zeros(on.size)
+    blk = on.block_view(U, 0)
+    vel = u0[:, None, None, None] + np.einsum("ab,kjib->akji", A, xc[..., :2])
+    p = 1.0 / G
+    blk[0, 0] = 1.0
+    blk[0, 1] = vel[0]
+    blk[0, 2] = vel[1]
+    blk[0, 3] = p / (G - 1) + 0.5 * (vel[0] ** 2 + vel[1] ** 2)
+    Rv = on.interior(on.residual(U, with_scale=False), 0) - off.interior(off.residual(U, with_scale=False), 0)
+    mu = 0.5 / 5.0e3
+    tau = mu * (A + A.T - 2.0 / 3.0 * np.trace(A) * np.eye(2))
+    phi = float(np.sum(tau * A))
+    _, _, g = on.blocks[0]
+    V = vol[:, g[1]:g[1] + nj, g[0]:g[0] + ni]
+    inner = (slice(None), slice(3, nj - 3), slice(3, ni - 3))   # cells whose stencils see no ghost
+    scale = mu * np.abs(A).max() * 2.2                          # |tau| |S| with |S| ~ 0.1
+    r = Rv[0]
+    assert np.abs(r[0][inner]).max() < 1e-12 * scale
+    assert np.abs(r[1][inner]).max() < 1e-9 * scale
+    assert np.abs(r[2][inner]).max() < 1e-9 * scale
+    np.testing.assert_allclose(r[3][inner], -V[inner] * phi, rtol=1e-8, atol=1e-9 * scale)
