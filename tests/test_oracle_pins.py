@@ -620,3 +620,48 @@ def test_viscous_flux_of_a_linear_velocity_field_is_exact_on_an_affine_grid():
     assert np.abs(r[1][inner]).max() < 1e-9 * scale
     assert np.abs(r[2][inner]).max() < 1e-9 * scale
     np.testing.assert_allclose(r[3][inner], -V[inner] * phi, rtol=1e-8, atol=1e-9 * scale)
+
+
+# ----------------------------------------------- viscous wall traction, Couette --
+def _couette_case(ni, nj, L, H):
+    """Uniform grid on [0, L] x [0, H], periodic in x; no-slip wall at y = 0
+    (body 0, at rest), slip wall at y = H; steady, laminar."""
+    X, Y = np.meshgrid(np.linspace(0.0, L, ni + 1), np.linspace(0.0, H, nj + 1))
+    ext = C.extend_ghost_nodes(np.stack([X, Y], axis=-1), 2, (True, False),
+                               period_shift=[np.array([L, 0.0]), np.zeros(2)])
+    side_bc = {(1, 0): (C.BC_NOSLIP, 0), (1, 1): (C.BC_SLIP, -1)}
+    bl, cuts, bcs = C.split_blocks(ext, 2, (ni, nj), (True, False), side_bc,
+                                   [C.BlockSpec((0, 0), (ni, nj))])
+    return C.Case(name="couette", dim=2, n_harm=0, mach=0.4, omega=0.1, viscous=True,
+                  blocks=bl, cuts=cuts, bcs=bcs, n_bodies=1, seed=1)
+
+
+def test_couette_wall_shear_gives_the_exact_skin_friction_force():
+    """Force reading (A14: wall pressure p_0, traction tau_w . S from the face
+    gradient, coefficients over 1/2 rho_inf U_inf^2 c with c = 1) and the
+    no-slip ghost u_g = -u: plane Couette flow u = U0 y / H over the wall at
+    rest, uniform density and pressure.  The mirrored ghosts continue the
+    linear profile, so the wall gradient is exact and the fluid pulls the
+    wall downstream with tau_xy = mu U0 / H over its length L: cd = mu U0 L /
+    (H q_inf), cl = 0 (no pressure excess, tau_yy = 0), cm = 0 (the force acts
+    on the line y = 0 through the pivot's height)."""
+    ni, nj, L, H, U0 = 16, 8, 1.0, 0.5, 0.3
+    cs = _couette_case(ni, nj, L, H)
+    o = Oracle(cs)
+    _, xc, _ = o.geometry(0)
+    U = np.zeros(o.size)
+    blk = o.block_view(U, 0)
+    u = U0 * xc[..., 1] / H
+    p = 1.0 / G
+    blk[0, 0] = 1.0
+    blk[0, 1] = u
+    blk[0, 2] = 0.0
+    blk[0, 3] = p / (G - 1) + 0.5 * u * u
+    coef, J = o.forces(U)
+    mu = cs.mach / cs.reynolds
+    qinf = 0.5 * cs.mach ** 2
+    cd = mu * U0 * L / (H * qinf)
+    cl_, cd_, cm_ = coef[0, 0]
+    assert abs(cd_ - cd) < 1e-12 * cd, (cd_, cd)
+    assert abs(cl_) < 1e-12 * cd and abs(cm_) < 1e-12 * cd, (cl_, cm_)
+    assert J == cl_
