@@ -665,3 +665,55 @@ def test_couette_wall_shear_gives_the_exact_skin_friction_force():
     assert abs(cd_ - cd) < 1e-12 * cd, (cd_, cd)
     assert abs(cl_) < 1e-12 * cd and abs(cm_) < 1e-12 * cd, (cl_, cm_)
     assert J == cl_
+
+
+# ------------------------------------------- farfield characteristic ghosts --
+def test_farfield_ghosts_carry_the_characteristic_invariants():
+    """Reading of the farfield condition (1D characteristics normal to the
+    face): the ghost state carries the outgoing Riemann invariant
+    R+ = q_n + 2c/(gamma-1) of the first interior cell and the incoming
+    R- = q_n - 2c/(gamma-1) of the freestream; entropy p / rho^gamma and the
+    tangential velocity come from the interior on outflow and from the
+    freestream on inflow; both ghost layers hold it.  Checked on the straight
+    inlet (x = 0) and outlet (x = 2) of the channel, steady, from a random
+    subsonic state around the freestream (M = 0.5, zero incidence)."""
+    cs = C.channel(24, 8, n_harm=0)
+    o = Oracle(cs)
+    rng = np.random.default_rng(3)
+    _, p_, g = o.blocks[0]
+    ni, nj = cs.blocks[0].n[0], cs.blocks[0].n[1]
+    U = np.zeros(o.size)
+    blk = o.block_view(U, 0)
+    sh = blk[0, 0].shape
+    rho = 1.0 + 0.05 * rng.uniform(-1, 1, sh)
+    u = 0.5 + 0.05 * rng.uniform(-1, 1, sh)
+    v = 0.05 * rng.uniform(-1, 1, sh)
+    p = (1.0 / G) * (1.0 + 0.05 * rng.uniform(-1, 1, sh))
+    blk[0, 0], blk[0, 1], blk[0, 2] = rho, rho * u, rho * v
+    blk[0, 3] = p / (G - 1) + 0.5 * rho * (u * u + v * v)
+    F = o.block_view(o.fill_ghosts(U), 0)[0, :, 0]           # [v][j][i], padded
+
+    def prim(i, j):
+        r = F[0, j, i]
+        uu, vv = F[1, j, i] / r, F[2, j, i] / r
+        pp = (G - 1) * (F[3, j, i] - 0.5 * r * (uu * uu + vv * vv))
+        return r, uu, vv, pp
+
+    Wf = (1.0, 0.5, 0.0, 1.0 / G)
+    for j in range(g[1], g[1] + nj):
+        for side, nx in ((0, -1.0), (1, 1.0)):                   # inlet: outward -x, outlet: +x
+            i_in = g[0] if side == 0 else g[0] + ni - 1
+            ghosts = (g[0] - 1, g[0] - 2) if side == 0 else (g[0] + ni, g[0] + ni + 1)
+            ri, ui, vi, pi = prim(i_in, j)
+            ci = math.sqrt(G * pi / ri)
+            cf = math.sqrt(G * Wf[3] / Wf[0])
+            Rp = nx * ui + 2 * ci / (G - 1)
+            Rm = nx * Wf[1] - 2 * cf / (G - 1)
+            src = (ri, ui, vi, pi) if side == 1 else Wf              # outflow at the outlet
+            for ig in ghosts:
+                rg, ug, vg, pg = prim(ig, j)
+                cg = math.sqrt(G * pg / rg)
+                assert abs(nx * ug + 2 * cg / (G - 1) - Rp) < 1e-12
+                assert abs(nx * ug - 2 * cg / (G - 1) - Rm) < 1e-12
+                assert abs(pg / rg ** G - src[3] / src[0] ** G) < 1e-12
+                assert abs(vg - src[2]) < 1e-12
