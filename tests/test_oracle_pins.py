@@ -717,3 +717,62 @@ def test_farfield_ghosts_carry_the_characteristic_invariants():
                 assert abs(nx * ug - 2 * cg / (G - 1) - Rm) < 1e-12
                 assert abs(pg / rg ** G - src[3] / src[0] ** G) < 1e-12
                 assert abs(vg - src[2]) < 1e-12
+
+
+# ------------------------------------------------ moving wall ghost kinematics --
+@pytest.mark.parametrize("viscous", [False, True])
+def test_pitching_wall_ghosts_satisfy_the_wall_condition(viscous):
+    """Wall readings (slip: relative normal velocity reflected; no-slip:
+    u_g = 2 v_wall - u) on a rigidly pitching O-grid.  Each ghost layer and
+    its mirror cell average to the wall's own velocity: the normal component
+    (slip) or the whole vector (no-slip) equals the velocity of the rotated
+    face midpoint, taken here as a central difference in time of the rigid
+    rotation x(t) = pivot + R(A sin(omega t)) (x - pivot), independent of the
+    oracle's grid-velocity formula; the slip wall keeps the tangential
+    velocity.  Every snapshot of N_H = 2, at each of which the pitch rate is
+    nonzero."""
+    cs = C.ogrid(32, 8, n_harm=2, viscous=viscous, pitch_deg=3.0, radius=5.0)
+    o = Oracle(cs)
+    rng = np.random.default_rng(4)
+    U = np.zeros(o.size)
+    blk = o.block_view(U, 0)
+    sh = blk[:, 0].shape
+    rho = 1.0 + 0.05 * rng.uniform(-1, 1, sh)
+    u = cs.mach + 0.05 * rng.uniform(-1, 1, sh)
+    v = 0.05 * rng.uniform(-1, 1, sh)
+    p = (1.0 / G) * (1.0 + 0.05 * rng.uniform(-1, 1, sh))
+    blk[:, 0], blk[:, 1], blk[:, 2] = rho, rho * u, rho * v
+    blk[:, 3] = p / (G - 1) + 0.5 * rho * (u * u + v * v)
+    Fv = o.block_view(o.fill_ghosts(U), 0)[:, :, 0]            # [n][v][j][i], padded
+    _, _, g = o.blocks[0]
+    nodes = cs.blocks[0].nodes                                   # [j][i][2], 2 ghost layers
+    A, w, ns = math.radians(cs.pitch_amp_deg), cs.omega, cs.n_snap
+    piv = np.array(cs.pivot)
+
+    def place(x, t):
+        th = A * math.sin(w * t)
+        R = np.array([[math.cos(th), -math.sin(th)], [math.sin(th), math.cos(th)]])
+        return piv + R @ (x - piv)
+
+    def vel(n, i, j):
+        return Fv[n, 1:3, j, i] / Fv[n, 0, j, i]
+
+    h = 1e-5
+    for n in range(ns):
+        t = 2 * math.pi * n / (ns * w)
+        for i in range(cs.blocks[0].n[0]):
+            x0, x1 = nodes[2, 2 + i], nodes[2, 3 + i]
+            xm = 0.5 * (x0 + x1)
+            vw = (place(xm, t + h) - place(xm, t - h)) / (2 * h)
+            e = place(x1, t) - place(x0, t)
+            nrm = np.array([e[1], -e[0]]) / np.linalg.norm(e)
+            tan = e / np.linalg.norm(e)
+            for layer in (1, 2):                                  # ghost g1-layer mirrors cell g1+layer-1
+                ug = vel(n, g[0] + i, g[1] - layer)
+                ui = vel(n, g[0] + i, g[1] + layer - 1)
+                mean = 0.5 * (ug + ui)
+                assert abs((mean - vw) @ nrm) < 1e-9, (n, i, layer)
+                if viscous:
+                    assert np.abs(mean - vw).max() < 1e-9, (n, i, layer)
+                else:
+                    assert abs((ug - ui) @ tan) < 1e-12, (n, i, layer)
