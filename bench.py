@@ -149,19 +149,20 @@ def run_reference(args):
 
 
 def cpu_baseline():
-    """The oracle on a bounded sample: 2 RK iterations of the same workload
-    family at 640 x 96 cells (a quarter of the cells), single thread."""
+    """The oracle on a bounded sample of the benchmark workload itself: one
+    RK iteration (4 stages) of the full 8-block 1280 x 192 NS O-grid, single
+    thread (about 10 s)."""
     from oracle.hb_oracle import Oracle, build
     from paper_1304_7654_gb300 import cases as C
     build()
-    cs = C.ns_ogrid8(640, 96)
+    cs = C.ns_ogrid8()
     o = Oracle(cs)
     U = o.init_state(C.noise(cs), 0.01)
     t = time.perf_counter()
-    o.rk_smooth(U, 2)
+    o.rk_smooth(U, 1)
     dt = time.perf_counter() - t
-    return {"value": cs.n_cells * cs.n_snap * 4 * 2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "2 RK iterations of the ns_ogrid8 family at 640x96 cells (61,440 cells, N_H=3), "
+    return {"value": cs.n_cells * cs.n_snap * 4 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 RK iteration of the full ns_ogrid8 workload (1280x192, {cs.n_cells:,} cells, N_H=3), "
                       f"single-threaded FP64, {dt:.1f} s"}
 
 
