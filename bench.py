@@ -595,7 +595,8 @@ def alu_roofline(name, units, launch_ms):
     achieved = rec["fp32_flops_per_unit"] * units / (launch_ms * 1e-3) / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_TFLOPS, "flops_per_unit": rec["fp32_flops_per_unit"],
-            "flops_source": "executed FP32 operations per cell-snapshot-stage (FFMA counted twice), ncu",
+            "flops_source": "executed FP32 operations per cell-snapshot-stage from ncu per-opcode counts "
+                            "(FFMA 2, FADD/FMUL 1, packed FFMA2 4, FADD2/FMUL2 2)",
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
 
 
