@@ -776,3 +776,48 @@ def test_pitching_wall_ghosts_satisfy_the_wall_condition(viscous):
                     assert np.abs(mean - vw).max() < 1e-9, (n, i, layer)
                 else:
                     assert abs((ug - ui) @ tan) < 1e-12, (n, i, layer)
+
+
+def test_viscous_flux_of_a_linear_velocity_field_is_exact_on_an_affine_grid_3d():
+    """The 3D form of the linear-field pin above: parallelepiped cells (an
+    affine map of a uniform lattice, ghosts point-reflected), u = u0 + A x
+    with a full 3x3 A, uniform density and pressure: the viscous part of each
+    interior residual is zero in mass and momentum and -V tau : A in energy,
+    tau = mu (A + A^T - 2/3 tr(A) I)."""
+    ni, nj, nk = 10, 9, 8
+    Z, Y, X = np.meshgrid(np.linspace(0, 1, nk + 1), np.linspace(0, 1, nj + 1), np.linspace(0, 1.2, ni + 1),
+                          indexing="ij")
+    M = np.array([[1.0, 0.2, 0.1], [0.05, 1.0, 0.15], [0.1, -0.1, 1.0]])
+    gn = np.einsum("ab,kjib->kjia", M, np.stack([X, Y, Z], axis=-1))
+    ext = C.extend_ghost_nodes(gn, 3, (False, False, False))
+    side_bc = {(d, s): (C.BC_FARFIELD, -1) for d in range(3) for s in range(2)}
+
+    def case(viscous):
+        bl, cuts, bcs = C.split_blocks(ext, 3, (ni, nj, nk), (False, False, False), side_bc,
+                                       [C.BlockSpec((0, 0, 0), (ni, nj, nk))])
+        return C.Case(name="affine_box", dim=3, n_harm=0, mach=0.3, omega=0.1, viscous=viscous,
+                      blocks=bl, cuts=cuts, bcs=bcs, n_bodies=0, seed=1)
+
+    A = np.array([[0.03, -0.02, 0.01], [0.05, 0.01, -0.04], [-0.02, 0.03, 0.02]])
+    u0 = np.array([0.3, 0.0, 0.0])
+    on, off = Oracle(case(True)), Oracle(case(False))
+    vol, xc, _ = on.geometry(0)
+    U = np.zeros(on.size)
+    blk = on.block_view(U, 0)
+    vel = u0[:, None, None, None] + np.einsum("ab,kjib->akji", A, xc)
+    p = 1.0 / G
+    blk[0, 0] = 1.0
+    blk[0, 1:4] = vel
+    blk[0, 4] = p / (G - 1) + 0.5 * (vel ** 2).sum(axis=0)
+    Rv = on.interior(on.residual(U, with_scale=False), 0) - off.interior(off.residual(U, with_scale=False), 0)
+    mu = 0.3 / 5.0e3
+    tau = mu * (A + A.T - 2.0 / 3.0 * np.trace(A) * np.eye(3))
+    phi = float(np.sum(tau * A))
+    _, _, g = on.blocks[0]
+    V = vol[g[2]:g[2] + nk, g[1]:g[1] + nj, g[0]:g[0] + ni]
+    inner = (slice(3, nk - 3), slice(3, nj - 3), slice(3, ni - 3))
+    scale = mu * np.abs(A).max() * 0.03                          # |tau| |S|, |S| ~ 0.015
+    r = Rv[0]
+    for q in range(4):
+        assert np.abs(r[q][inner]).max() < 1e-9 * scale, q
+    np.testing.assert_allclose(r[4][inner], -V[inner] * phi, rtol=1e-8, atol=1e-9 * scale)
