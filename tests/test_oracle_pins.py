@@ -821,3 +821,174 @@ def test_viscous_flux_of_a_linear_velocity_field_is_exact_on_an_affine_grid_3d()
     for q in range(4):
         assert np.abs(r[q][inner]).max() < 1e-9 * scale, q
     np.testing.assert_allclose(r[4][inner], -V[inner] * phi, rtol=1e-8, atol=1e-9 * scale)
+
+
+# ------------------------------------- unsteady farfield: inlet angle and gust --
+def _ff_ghost_checks(Wg, Wi, Winf, nrm):
+    """Deviations of a farfield ghost from the characteristic reading, as a
+    vector: [R+ of the ghost - R+ of the interior cell, R- of the ghost - R- of
+    the freestream, entropy - upwind entropy, tangential velocity - upwind
+    tangential velocity (3 comps)].  The upwind side is chosen by the sign of
+    the ghost's own normal velocity (outflow: interior, inflow: freestream)."""
+    def inv(W):
+        rho, vel, p = W[0], np.asarray(W[1:4]), W[4]
+        q = vel @ nrm
+        c = math.sqrt(G * p / rho)
+        return q + 2 * c / (G - 1), q - 2 * c / (G - 1), p / rho ** G, vel - q * nrm
+    gp, gm, gs, gt = inv(Wg)
+    ip, _, is_, it = inv(Wi)
+    _, fm, fs, ft = inv(Winf)
+    up_s, up_t = (is_, it) if (np.asarray(Wg[1:4]) @ nrm) > 0 else (fs, ft)
+    return np.concatenate([[gp - ip, gm - fm, gs - up_s], gt - up_t])
+
+
+def _prim5(Uc, dim):
+    rho = Uc[0]
+    vel = np.zeros(3)
+    vel[:dim] = Uc[1:1 + dim] / rho
+    p = (G - 1) * (Uc[dim + 1] - 0.5 * rho * vel @ vel)
+    return np.array([rho, *vel, p])
+
+
+def _random_state_around(o, cs, rng, u0, amp=0.05):
+    U = np.zeros(o.size)
+    for b in range(len(cs.blocks)):
+        blk = o.block_view(U, b)
+        sh = blk[:, 0].shape
+        rho = 1.0 + amp * rng.uniform(-1, 1, sh)
+        vel = [u0[a] + amp * rng.uniform(-1, 1, sh) for a in range(cs.dim)]
+        p = (1.0 / G) * (1.0 + amp * rng.uniform(-1, 1, sh))
+        blk[:, 0] = rho
+        for a in range(cs.dim):
+            blk[:, 1 + a] = rho * vel[a]
+        blk[:, cs.dim + 1] = p / (G - 1) + 0.5 * rho * sum(v * v for v in vel)
+    return U
+
+
+def _channel_inflow_freestream(cs, n, mutation=None):
+    """Freestream of snapshot n of the 2D channel workload, written from the
+    workload's statement: inlet angle alpha(t) = 2 deg * sin(omega t) with
+    omega from reduced frequency 0.1 on the unit height (omega = 0.2 M),
+    t_n = 2 pi n / (N_s omega); rho = 1, c = 1, |u| = M."""
+    M = cs.mach
+    w = 0.2 * M
+    t = 2 * math.pi * n / (cs.n_snap * w)
+    amp = math.radians(2.0)
+    if mutation == "deg_as_rad":
+        amp = 2.0
+    elif mutation == "amplitude":
+        amp = math.radians(2.0) * 1.5
+    elif mutation == "phase_sign":
+        t = -t
+    a = amp * math.sin(w * t)
+    return np.array([1.0, M * math.cos(a), M * math.sin(a), 0.0, 1.0 / G])
+
+
+def _channel_farfield_deviation(mutation=None):
+    cs = C.channel(24, 8, n_harm=2)
+    o = Oracle(cs)
+    U = _random_state_around(o, cs, np.random.default_rng(13), (cs.mach, 0.0))
+    F = o.block_view(o.fill_ghosts(U), 0)[:, :, 0]              # [n][v][j][i], padded
+    _, _, g = o.blocks[0]
+    ni, nj = cs.blocks[0].n[0], cs.blocks[0].n[1]
+    worst = 0.0
+    for n in range(cs.n_snap):
+        Winf = _channel_inflow_freestream(cs, n, mutation)
+        for j in range(g[1], g[1] + nj):
+            for side, nx in ((0, -1.0), (1, 1.0)):                 # x = 0 and x = 2 are straight
+                i_in = g[0] if side == 0 else g[0] + ni - 1
+                ghosts = (g[0] - 1, g[0] - 2) if side == 0 else (g[0] + ni, g[0] + ni + 1)
+                Wi = _prim5(F[n, :, j, i_in], 2)
+                for ig in ghosts:
+                    dev = _ff_ghost_checks(_prim5(F[n, :, j, ig], 2), Wi, Winf, np.array([nx, 0.0, 0.0]))
+                    worst = max(worst, np.abs(dev).max())
+    return worst
+
+
+def test_unsteady_inlet_angle_farfield_ghosts():
+    """Channel workload (inlet angle 2 deg sin(omega t), Mach 0.5, reduced
+    frequency 0.1 on the height): at every snapshot of N_H = 2 the farfield
+    ghosts at inlet and outlet carry the freestream's incoming invariant, and
+    on inflow its entropy and tangential velocity, of the inflow angle of that
+    snapshot.  The expected freestream is computed here from the workload's
+    statement, not by the oracle."""
+    assert _channel_farfield_deviation() < 1e-12
+
+
+@pytest.mark.parametrize("mutation", ["deg_as_rad", "amplitude", "phase_sign"])
+def test_unsteady_inlet_angle_pin_detects_planted_mistakes(mutation):
+    """The same check against a freestream carrying a plausible mistake (the
+    2 deg amplitude read as radians, a wrong amplitude, the time phase with
+    the wrong sign) fails by far: the pin separates them from the reading."""
+    assert _channel_farfield_deviation(mutation) > 1e-4
+
+
+def _box_gust_freestream(cs, n, xf, mutation=None):
+    """Freestream of snapshot n of the 3D box workload at a point with
+    x-coordinate xf: a convected vertical gust v' = 0.02 M sin(omega t -
+    omega x / M) on the uniform stream (M, 0, 0); omega = 0.2 M."""
+    M = cs.mach
+    w = 0.2 * M
+    t = 2 * math.pi * n / (cs.n_snap * w)
+    amp = 0.02 * M
+    ph = w * t - w * xf / M
+    if mutation == "amplitude":
+        amp = 0.02
+    elif mutation == "phase_sign":
+        ph = w * t + w * xf / M
+    elif mutation == "deg_as_rad":
+        ph = math.radians(ph)
+    return np.array([1.0, M, amp * math.sin(ph), 0.0, 1.0 / G])
+
+
+def _box_farfield_deviation(mutation=None):
+    cs = C.box3d(8, 6, 4, n_harm=2)
+    o = Oracle(cs)
+    U = _random_state_around(o, cs, np.random.default_rng(14), (cs.mach, 0.0, 0.0), amp=0.004)
+    F = o.block_view(o.fill_ghosts(U), 0)                       # [n][v][k][j][i], padded
+    _, _, g = o.blocks[0]
+    ni, nj, nk = cs.blocks[0].n
+    X = cs.blocks[0].nodes                                       # [k][j][i][3], 2 ghost layers
+    worst = 0.0
+    for n in range(cs.n_snap):
+        for k in range(nk):
+            kk = g[2] + k
+            # x-min and x-max faces (straight planes x = 0 and x = 4)
+            for j in range(nj):
+                jj = g[1] + j
+                for side, nx in ((0, -1.0), (1, 1.0)):
+                    a = 2 if side == 0 else 2 + ni                 # node index of the face plane
+                    xf = X[2 + k:4 + k, 2 + j:4 + j, a, 0].mean()
+                    Winf = _box_gust_freestream(cs, n, xf, mutation)
+                    i_in = g[0] if side == 0 else g[0] + ni - 1
+                    Wi = _prim5(F[n, :, kk, jj, i_in], 3)
+                    for ig in ((g[0] - 1, g[0] - 2) if side == 0 else (g[0] + ni, g[0] + ni + 1)):
+                        dev = _ff_ghost_checks(_prim5(F[n, :, kk, jj, ig], 3), Wi, Winf,
+                                               np.array([nx, 0.0, 0.0]))
+                        worst = max(worst, np.abs(dev).max())
+            # y-max face (the plane y = 1), normal +y: the gust is the normal velocity
+            for i in range(ni):
+                ii = g[0] + i
+                xf = X[2 + k:4 + k, 2 + nj, 2 + i:4 + i, 0].mean()
+                Winf = _box_gust_freestream(cs, n, xf, mutation)
+                Wi = _prim5(F[n, :, kk, g[1] + nj - 1, ii], 3)
+                for jg in (g[1] + nj, g[1] + nj + 1):
+                    dev = _ff_ghost_checks(_prim5(F[n, :, kk, jg, ii], 3), Wi, Winf, np.array([0.0, 1.0, 0.0]))
+                    worst = max(worst, np.abs(dev).max())
+    return worst
+
+
+def test_convected_gust_farfield_ghosts():
+    """3D box workload (vertical gust 0.02 M sin(omega t - omega x / M) at the
+    farfield, Mach 0.3, omega = 0.2 M): at every snapshot of N_H = 2 the
+    ghosts at x = 0, x = 4 and y = 1 carry the incoming invariant of the gusty
+    freestream at the face centroid, and on inflow its entropy and tangential
+    velocity; expected values from the workload's statement."""
+    assert _box_farfield_deviation() < 1e-12
+
+
+@pytest.mark.parametrize("mutation", ["deg_as_rad", "amplitude", "phase_sign"])
+def test_convected_gust_pin_detects_planted_mistakes(mutation):
+    """Gust amplitude without the factor M, the convective phase with the
+    wrong sign, and the phase taken as degrees each fail the check."""
+    assert _box_farfield_deviation(mutation) > 1e-5
