@@ -283,9 +283,16 @@ def ogrid_nodes(ni: int, nj: int, radius=20.0, first=1.0e-3):
     """O-grid nodes [j, i, 2] around a closed-TE NACA-0012-thickness body.
 
     i runs clockwise from the trailing edge (lower surface first) so that
-    (i, j-outward) is right-handed; node column ni repeats column 0."""
+    (i, j-outward) is right-handed; node column ni repeats column 0.  Surface
+    nodes sit at x = 1 - |sin(beta/2)|: clustered at the leading edge and
+    evenly spaced (dx ~ dbeta/2) at the sharp trailing edge.  With that
+    spacing the straight grid lines of neighbouring trailing-edge nodes meet
+    only ~0.07 c inside the body, so the point-reflected ghost cells (two
+    layers of ~1e-3 c) keep positive volumes; a cosine distribution, clustered
+    at both ends, makes them meet within 2e-4 c and inverts the ghost cells
+    at the trailing edge."""
     beta = -2.0 * np.pi * np.arange(ni + 1) / ni
-    xs = 0.5 * (1.0 + np.cos(beta))
+    xs = 1.0 - np.abs(np.sin(0.5 * beta))
     ys = np.sign(np.sin(beta)) * naca0012_closed(xs)
     xo = 0.5 + radius * np.cos(beta)
     yo = radius * np.sin(beta)
