@@ -109,61 +109,105 @@ def _cpu_cores():
 
 
 # ------------------------------------------------------------ reference arm --
+def _cpu_model():
+    """Host CPU model (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+def _oracle_threads():
+    """The OpenMP build of the oracle and the host cores it may use."""
+    from oracle.hb_oracle import build, build_openmp
+    build()
+    build_openmp()
+    return _cpu_cores()
+
+
 def run_reference(args):
-    """FP64 CPU oracle as it stands, single thread: each step is one RK
-    iteration of the same 8-block NS O-grid family on a bounded sample of the
-    cells (320 x 48, or 160 x 48 / 80 x 48 when that many steps would take
-    more than about two minutes at ~0.6 s per 320 x 48 step), timed on the
+    """FP64 CPU oracle as it stands, with its residual sweeps over (block,
+    snapshot) rows on all host cores (OpenMP build, the same result bit for
+    bit as one thread): each step is one RK iteration of the benchmark
+    workload, the full 8-block 1280 x 192 NS O-grid when the whole run fits in
+    about two minutes, else a smaller member of the same family, timed on the
     host clock."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
-    import numpy as np
-    from oracle.hb_oracle import Oracle, build
+    from oracle.hb_oracle import Oracle
     from paper_1304_7654_gb300 import cases as C
-    build()
-    ni = 320
-    while ni > 80 and (args.steps + args.warmup) * 0.65 * ni / 320 > 120:
-        ni //= 2
-    cs = C.ns_ogrid8(ni, 48)
-    o = Oracle(cs)
+    cores = _oracle_threads()
+    ni, nj = 1280, 192
+    cs = C.ns_ogrid8(ni, nj)
+    o = Oracle(cs, openmp=True)
     U = o.init_state(C.noise(cs), 0.01)
-    for _ in range(args.warmup):
-        U, _ = o.rk_smooth(U, 1)
+    t = time.perf_counter()
+    U, _ = o.rk_smooth_threads(U, 1, cores)            # first warm-up step, timed to size the sample
+    t1 = time.perf_counter() - t
+    while ni > 80 and (args.steps + args.warmup) * t1 > 120:
+        ni //= 2
+        nj = max(24, nj // 2)
+        t1 /= 4
+    if ni != 1280:
+        cs = C.ns_ogrid8(ni, nj)
+        o = Oracle(cs, openmp=True)
+        U = o.init_state(C.noise(cs), 0.01)
+    for _ in range(args.warmup - (1 if ni == 1280 else 0)):
+        U, _ = o.rk_smooth_threads(U, 1, cores)
     t = time.perf_counter()
     for _ in range(args.steps):
-        U, _ = o.rk_smooth(U, 1)
+        U, _ = o.rk_smooth_threads(U, 1, cores)
     dt = time.perf_counter() - t
     units = cs.n_cells * cs.n_snap * 4 * args.steps
     val = units / dt
-    sample = (f"one RK iteration per step of the ns_ogrid8 family at {ni}x48 cells ({cs.n_cells:,} cells, "
-              "N_H=3), single-threaded FP64 oracle")
+    sample = (f"one RK iteration per step of the ns_ogrid8 family at {ni}x{nj} cells ({cs.n_cells:,} cells, "
+              f"N_H=3), FP64 oracle, residual sweeps on {cores} threads ({_cpu_model()})")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(WORKLOAD, sample=sample),
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": dict(WORKLOAD, sample=sample, same_config=(ni == 1280)),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
 def cpu_baseline():
-    """The oracle on a bounded sample of the benchmark workload itself: one
-    RK iteration (4 stages) of the full 8-block 1280 x 192 NS O-grid, single
-    thread (about 10 s)."""
-    from oracle.hb_oracle import Oracle, build
+    """The oracle on a bounded sample of the benchmark workload itself: one RK
+    iteration (4 stages) of the full 8-block 1280 x 192 NS O-grid on all host
+    cores (OpenMP build over (block, snapshot) rows; about 1-2 s on 16 cores)
+    and on one thread (about 10 s)."""
+    from oracle.hb_oracle import Oracle
     from paper_1304_7654_gb300 import cases as C
-    build()
+    cores = _oracle_threads()
     cs = C.ns_ogrid8()
-    o = Oracle(cs)
+    o = Oracle(cs, openmp=True)
     U = o.init_state(C.noise(cs), 0.01)
+    units = cs.n_cells * cs.n_snap * 4
     t = time.perf_counter()
-    o.rk_smooth(U, 1)
-    dt = time.perf_counter() - t
-    return {"value": cs.n_cells * cs.n_snap * 4 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    o.rk_smooth_threads(U, 1, cores)
+    dt_n = time.perf_counter() - t
+    t = time.perf_counter()
+    o.rk_smooth_threads(U, 1, 1)
+    dt_1 = time.perf_counter() - t
+    model = _cpu_model()
+    return {"value": units / dt_n, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"1 RK iteration of the full ns_ogrid8 workload (1280x192, {cs.n_cells:,} cells, N_H=3), "
-                      f"single-threaded FP64, {dt:.1f} s"}
+                      f"FP64, residual sweeps over (block, snapshot) rows on {cores} threads, {dt_n:.2f} s",
+            "host_cores": cores, "cpu_model": model,
+            "single_thread": {"value": units / dt_1, "unit": UNIT, "cores": 1, "seconds": dt_1}}
 
 
 # --------------------------------------------------------------- our arm --
@@ -185,15 +229,14 @@ def replica_throughput(world_size, units_per_rank_step, ms_per_step):
     return world_size * units_per_rank_step / (ms_per_step * 1e-3)
 
 
-def algorithmic_bytes_per_unit(nv, s, moving, viscous, ns):
-    """Bytes one cell-snapshot-stage must move, averaged over the 4 stages:
-    stage 1 reads U and writes U1 (2 nv s); stages 2-4 read U^(s-1), U^(0) and
-    write (3 nv s); plus the static metrics each stage reads once per cell for
-    all snapshots: volume, 2 face vectors (4), centre differences (4, viscous),
-    the faces' grid-velocity factors (2) and the centre (2) (pitching grids)."""
+def algorithmic_bytes_per_unit(nv, s, dim, ns):
+    """Algorithmic bytes of one cell-snapshot-stage, averaged over the 4
+    stages of a fused RK iteration: stage 1 reads U and writes U1 (2 nv s);
+    stages 2-4 read U^(s-1) and U^(0) and write (3 nv s); the grid enters as
+    its nodes (dim values per cell), read once per stage for all N_s
+    snapshots.  FP32 2D, N_s = 7: 44 + 8/7 = 45.1 B."""
     state = (2 + 3 + 3 + 3) / 4.0 * nv * s
-    geo = 1 + 4 + (4 if viscous else 0) + (4 if moving else 0)
-    return state + geo * s / ns
+    return state + dim * s / ns
 
 
 def _checked_status(ctx, what):
@@ -218,7 +261,8 @@ def roofline(peaks, src, bpu_stage, cells_snaps, mode, launch_ms, kernel, traffi
     units = cells_snaps * stages
     achieved = bpu_stage * units / (launch_ms * 1e-3) / 1e9 if launch_ms > 0 else 0.0
     return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kernel,
+            "frac": achieved / peaks["hbm_gbs"], "frac_of_nominal_8TBs": achieved / 8000.0,
+            "traffic": traffic, "kernel": kernel,
             "peak_source": src, "bytes_per_unit": bpu_stage, "unit_def": "cell-snapshot-stage",
             "units_per_launch": units, "launch_ms": launch_ms}
 
@@ -307,7 +351,8 @@ def run_ours(args):
     r32 = run_prec("fp32", args.steps, args.warmup)
     clk = clocks.stop()
     # FP64 plain path on the same workload, for comparison (one launch per phase)
-    r64 = run_prec("fp64", args.fp64_steps, 2, tune=False)
+    fp64_steps = args.fp64_steps or max(3, min(args.steps, 20))
+    r64 = run_prec("fp64", fp64_steps, 2, tune=False)
     batch = run_batch(args, dev) if not args.no_batch else None
     adj = adjoint_ratio(dev) if not args.no_adjoint else None
     box = run_box3d(args, dev) if not args.no_batch else None
@@ -352,10 +397,10 @@ def run_ours(args):
     ms32, e2e_ms = max_over_ranks([r32["ms"], e2e_ms], dev)
     ms_per_step = ms32 / args.steps
     value = replica_throughput(ws, units_per_step, ms_per_step)
-    v64 = units_per_step / (r64["ms"] / args.fp64_steps * 1e-3)
+    v64 = units_per_step / (r64["ms"] / fp64_steps * 1e-3)
 
     peaks, src = _peaks()
-    bpu = algorithmic_bytes_per_unit(cs.nv, 4, True, True, cs.n_snap)
+    bpu = algorithmic_bytes_per_unit(cs.nv, 4, cs.dim, cs.n_snap)
     mode, TI, TJ = r32["tuning"]
     launch_ms = r32["tile_ms"] / max(1, r32["tile_n"])
     kname = (f"persist_kernel<float,VISC,{TI},{TJ}>" if mode & 1 else f"tile2d_kernel<float,7,VISC,RK,{TI},{TJ}>")
@@ -378,9 +423,13 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(host_out.numel() * host_out.element_size())},
             "gpu_launches": int(r32["launches"]),
             "clocks": clk,
-            "fp64_plain": {"value": v64, "unit": UNIT, "ms_per_step": r64["ms"] / args.fp64_steps,
-                           "steps": args.fp64_steps,
-                           "tile_launch_ms": r64["tile_ms"] / max(1, r64["tile_n"])},
+            "useful_GBs": bpu * value / 1e9,
+            "binding_roof": binding_roof(peaks, bpu, f"{'persist' if mode & 1 else 'tile2d'}_f32_{TI}x{TJ}_ns_ogrid8"),
+            "fp64_plain": {"value": v64, "unit": UNIT, "ms_per_step": r64["ms"] / fp64_steps,
+                           "steps": fp64_steps,
+                           "tile_launch_ms": r64["tile_ms"] / max(1, r64["tile_n"]),
+                           "roofline_fp64": fp64_roofline("tile2d_f64_32x8_ns_ogrid8", cs.n_cells * cs.n_snap,
+                                                          r64["tile_ms"] / max(1, r64["tile_n"]))},
             "fp32_over_fp64": value / ws / v64,
             "tuning": _tuning_desc(mode, TI, TJ),
             "batched_fp32": batch,
@@ -421,9 +470,26 @@ def run_batch(args, dev):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / K
     units = sum(c.n_cells * c.n_snap for c in cases) * 4
+    cap, replays, persist_replays, direct = ctx.graph_info()
+    # algorithmic bytes of one iteration of the mixed-N_s batch (4 stages per
+    # cell-snapshot, each case with its own N_s) over the measured iteration
+    it_bytes = sum(4 * algorithmic_bytes_per_unit(c.nv, 4, c.dim, c.n_snap) * c.n_cells * c.n_snap for c in cases)
+    peaks, src = _peaks()
+    achieved = it_bytes / (ms * 1e-3) / 1e9
+    kname = f"persist_kernel<float,0,{TI},{TJ}>" if mode & 1 else f"tile2d_kernel<float,NS,0,RK,{TI},{TJ}>"
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "frac_of_nominal_8TBs": achieved / 8000.0,
+            "traffic": _traffic_record(f"persist_f32_{TI}x{TJ}_batch64") if mode & 1 else None,
+            "kernel": kname, "peak_source": src,
+            "bytes_per_iteration": it_bytes, "units_per_iteration": units,
+            "time_basis": "CUDA events around K iterations replayed from the captured persistent-launch graph"}
     return {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_iteration": ms, "iterations": K,
             "cases": len(cases), "cells": int(sum(c.n_cells for c in cases)),
             "cell_snapshots": int(sum(c.n_cells * c.n_snap for c in cases)),
+            "roofline": roof,
+            "l2": "not flushed: the batch state (~150 MB FP32 plus the RK buffers) exceeds the 129 MB L2",
+            "graph": {"persistent_chunk_captured": cap, "graph_replays": replays,
+                      "persistent_replays": persist_replays, "persistent_direct_launches": direct},
             **_tuning_desc(mode, TI, TJ),
             "status": _checked_status(ctx, "batched FP32")}
 
@@ -462,7 +528,7 @@ def run_paper_shapes(args, dev):
         ms = a.elapsed_time(b) / steps
         units = cs.n_cells * cs.n_snap * 4
         tl = tile_ms / max(1, tile_n)
-        bpu = algorithmic_bytes_per_unit(cs.nv, 4, cs.motion != 0, cs.viscous, cs.n_snap)
+        bpu = algorithmic_bytes_per_unit(cs.nv, 4, cs.dim, cs.n_snap)
         peaks, _ = _peaks()
         out[name] = {"value": units / (ms * 1e-3), "unit": UNIT, "ms_per_iteration": ms, "iterations": steps,
                      "cells": cs.n_cells, "blocks": len(cs.blocks), "n_snap": cs.n_snap,
@@ -506,7 +572,7 @@ def run_box3d(args, dev):
     ms = a.elapsed_time(b) / steps
     cells_snaps = cs.n_cells * cs.n_snap
     nv, s = 5, 4
-    tile_bytes = ((2 + 3 + 3 + 3) / 4.0 * nv * s + (1 + 9 + 9) * s / cs.n_snap) * cells_snaps
+    tile_bytes = algorithmic_bytes_per_unit(nv, s, 3, cs.n_snap) * cells_snaps
     ghosts = sum((b_.n[0] + 4) * (b_.n[1] + 4) * (b_.n[2] + 4) - b_.n[0] * b_.n[1] * b_.n[2] for b_ in cs.blocks)
     halo_bytes = 2 * ghosts * nv * s * cs.n_snap / 3.0            # per pass, three passes per stage
     tl = tile_ms / max(1, tile_n)
@@ -600,6 +666,38 @@ def alu_roofline(name, units, launch_ms):
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
 
 
+# FP64 pipe: about 2 DFMA lanes per clock per SM on this part (ncu pipe
+# utilisation of the FP64 tile kernel), 152 SMs x 2 x 2 flops x 2.07 GHz,
+# consistent with the nominal 1.25 TFLOP/s
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def fp64_roofline(name, units, launch_ms):
+    """The FP64 tile kernel against the FP64 pipe: executed FP64 operations per
+    cell-snapshot-stage from the committed ncu record over the launch time."""
+    rec = _profile_record(name)
+    if not rec or "fp64_flops_per_unit" not in rec or launch_ms <= 0:
+        return None
+    achieved = rec["fp64_flops_per_unit"] * units / (launch_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "flops_per_unit": rec["fp64_flops_per_unit"],
+            "flops_source": "executed FP64 operations per cell-snapshot-stage from ncu per-opcode counts "
+                            "(DFMA 2, DADD/DMUL 1)",
+            "peak_source": "derived: 152 SMs x 2 DFMA lanes x 2 x 2.07 GHz"}
+
+
+def binding_roof(peaks, bpu, name):
+    """Which roof caps the FP32 tile kernel: cell-snapshot-stages per second
+    at the HBM roof (algorithmic bytes) and at the FP32 arithmetic roof
+    (executed flops from the committed ncu record); the lower one binds."""
+    hbm = peaks["hbm_gbs"] * 1e9 / bpu
+    rec = _profile_record(name)
+    if not rec or "fp32_flops_per_unit" not in rec:
+        return {"bound": "hbm", "hbm_cap_units_per_s": hbm, "alu_cap_units_per_s": None}
+    alu = FP32_PEAK_TFLOPS * 1e12 / rec["fp32_flops_per_unit"]
+    return {"bound": "alu" if alu < hbm else "hbm", "hbm_cap_units_per_s": hbm, "alu_cap_units_per_s": alu}
+
+
 def _traffic_record(name):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, if it was taken on the current kernel source."""
@@ -685,7 +783,8 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="timed steps of the FP64 plain path (default: min(steps, 20))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")

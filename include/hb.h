@@ -234,6 +234,17 @@ hb_status hb_get_tuning(const hb_ctx* ctx, int* mode, int* TI, int* TJ);
 hb_status hb_set_timing(hb_ctx* ctx, int enable);
 hb_status hb_kernel_stats(hb_ctx* ctx, int which, double* ms, int64_t* launches, int reset);
 
+/* Which driver form hb_rk_smooth used.  *persist_captured: -1 while no
+ * persistent chunk has run, 1 once a persistent chunk (one cooperative launch
+ * for all cases and all stages of up to 64 iterations) was captured into a
+ * CUDA graph, 0 if that capture failed and such chunks run as direct
+ * cooperative launches.  counts (may be NULL): [0] RK chunks replayed from a
+ * captured graph, [1] those that were persistent chunks, [2] persistent
+ * chunks launched directly (capture refused, or timing enabled); cumulative
+ * since hb_create.  Paper counterpart: none (the paper's drivers are MPI
+ * processes; this reports how the batched single-GPU form was launched). */
+hb_status hb_graph_info(const hb_ctx* ctx, int* persist_captured, int64_t counts[3]);
+
 /* Limits of hb_residual_norms_noalloc's fixed scratch. */
 #define HB_NOALLOC_MAX_CTAS 2048
 #define HB_NOALLOC_MAX_VARS 8

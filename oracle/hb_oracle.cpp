@@ -24,6 +24,9 @@
 // recomputed from both sides, every gradient from scratch: slow and plain.
 #include <algorithm>
 #include <array>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -474,11 +477,12 @@ void face_flux(const Case& C, const S* U, int b, int n, const Frame& f, int d, c
 
 // HB residual of one interior cell at all snapshots: R[n][v]; optional scale[n][v]
 // = sum of |face flux| + |HB source| (the magnitude the residual cancels)
+// residual of cell (b, i, j, k) at snapshot n: R[v], scale[v] for v < nv
 template <class S>
-void cell_residual(const Case& C, const S* U, int b, int i, int j, int k, S* R, double* scale) {
+void snapshot_residual(const Case& C, const S* U, int b, int i, int j, int k, int n, S* R, double* scale) {
   const Block& B = C.B[b];
   int64_t c = B.cell(i, j, k);
-  for (int n = 0; n < C.ns; ++n) {
+  {
     Frame f = frame(C, n);
     S acc[5];
     for (int q = 0; q < 5; ++q) acc[q] = S(0.0);
@@ -498,10 +502,17 @@ void cell_residual(const Case& C, const S* U, int b, int i, int j, int k, S* R, 
       S hb = S(0.0);
       for (int m = 0; m < C.ns; ++m) hb += C.D[n * C.ns + m] * U[C.at(b, m, v, c)];
       hb = B.vol[c] * C.omega * hb;
-      R[n * C.nv + v] = acc[comp5(C, v)] + hb;
-      if (scale) scale[n * C.nv + v] = sc[comp5(C, v)] + std::fabs(val(hb));
+      R[v] = acc[comp5(C, v)] + hb;
+      if (scale) scale[v] = sc[comp5(C, v)] + std::fabs(val(hb));
     }
   }
+}
+
+// residual of cell (b, i, j, k) at every snapshot: R[n * nv + v]
+template <class S>
+void cell_residual(const Case& C, const S* U, int b, int i, int j, int k, S* R, double* scale) {
+  for (int n = 0; n < C.ns; ++n)
+    snapshot_residual(C, U, b, i, j, k, n, R + n * C.nv, scale ? scale + n * C.nv : nullptr);
 }
 
 // ------------------------------------------------------- ghost filling --
@@ -881,16 +892,44 @@ void orc_time_step(void* h, const double* U, double* dt) {
   });
 }
 
+namespace {
+// The residual sweep of a stage: every (block, snapshot) pair, split into
+// rows of cells.  With threads > 1 (a library built with OpenMP) the items
+// run on that many threads, the hybrid harmonic parallelisation the paper
+// applies with OpenMP (Sec. 2): each item writes only its own entries of R,
+// so the result is bit for bit the single-thread one.
+void residual_sweep(const Case& C, const double* U, double* R, int threads) {
+  struct Item { int b, n, j, k; };
+  std::vector<Item> items;
+  for (int b = 0; b < (int)C.B.size(); ++b)
+    for (int n = 0; n < C.ns; ++n)
+      for (int k = 0; k < C.B[b].n[2]; ++k)
+        for (int j = 0; j < C.B[b].n[1]; ++j) items.push_back({b, n, j, k});
+  const int64_t count = (int64_t)items.size();
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4) num_threads(threads > 0 ? threads : 1)
+#endif
+  for (int64_t q = 0; q < count; ++q) {
+    const Item& it = items[q];
+    const Block& B = C.B[it.b];
+    double r[5];
+    for (int i = 0; i < B.n[0]; ++i) {
+      snapshot_residual(C, U, it.b, i, it.j, it.k, it.n, r, (double*)nullptr);
+      int64_t c = B.cell(i, it.j, it.k);
+      for (int v = 0; v < C.nv; ++v) R[C.at(it.b, it.n, v, c)] = r[v];
+    }
+  }
+  (void)threads;
+}
+
 // n_iter iterations of the 4-stage Runge-Kutta smoother with local time steps
 // (coefficients 1/4, 1/3, 1/2, 1); norms[it][v] = RMS of R/V over interior
 // cells and snapshots at the first stage, or NULL
-void orc_rk_smooth(void* h, double* U, int n_iter, double* norms) {
-  Case* C = (Case*)h;
+void rk_smooth(Case* C, double* U, int n_iter, double* norms, int threads) {
   const double alpha[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
   std::vector<double> U0(C->total), dt(C->total), R(C->total);
   int64_t ncells = 0;
   for (auto& B : C->B) ncells += (int64_t)B.n[0] * B.n[1] * B.n[2];
-  std::vector<double> r(C->ns * C->nv);
   for (int it = 0; it < n_iter; ++it) {
     std::copy(U, U + C->total, U0.begin());
     for_interior(*C, [&](int b, int i, int j, int k) {
@@ -900,12 +939,7 @@ void orc_rk_smooth(void* h, double* U, int n_iter, double* norms) {
     for (int s = 0; s < 4; ++s) {
       fill_ghosts(*C, U);
       double acc[5] = {0, 0, 0, 0, 0};
-      for_interior(*C, [&](int b, int i, int j, int k) {
-        cell_residual(*C, (const double*)U, b, i, j, k, r.data(), (double*)nullptr);
-        int64_t c = C->B[b].cell(i, j, k);
-        for (int n = 0; n < C->ns; ++n)
-          for (int v = 0; v < C->nv; ++v) R[C->at(b, n, v, c)] = r[n * C->nv + v];
-      });
+      residual_sweep(*C, (const double*)U, R.data(), threads);
       for_interior(*C, [&](int b, int i, int j, int k) {
         int64_t c = C->B[b].cell(i, j, k);
         double V = C->B[b].vol[c];
@@ -923,6 +957,26 @@ void orc_rk_smooth(void* h, double* U, int n_iter, double* norms) {
           norms[(int64_t)it * C->nv + v] = std::sqrt(acc[v] / (double)(ncells * C->ns));
     }
   }
+}
+}  // namespace
+
+void orc_rk_smooth(void* h, double* U, int n_iter, double* norms) {
+  rk_smooth((Case*)h, U, n_iter, norms, 1);
+}
+
+// the same iterations with the residual sweeps on `threads` threads (only in
+// the OpenMP build of this file; otherwise one thread): the same result, bit
+// for bit.  orc_openmp_threads reports the threads available (0 without OpenMP).
+void orc_rk_smooth_threads(void* h, double* U, int n_iter, double* norms, int threads) {
+  rk_smooth((Case*)h, U, n_iter, norms, threads);
+}
+
+int orc_openmp_threads() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 0;
+#endif
 }
 
 // ---- time-domain dual time stepping (a case with one snapshot).  Reading:

@@ -21,28 +21,41 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hb_oracle.cpp")
 _LIB = os.path.join(_HERE, "libhb_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "libhb_oracle_omp.so")
 _lock = threading.Lock()
 _lib = None
+_lib_omp = None
 
 _dp = ct.POINTER(ct.c_double)
 _ip = ct.POINTER(ct.c_int)
 
 
+def _compile(lib: str, extra, force: bool) -> str:
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + f".tmp{os.getpid()}"
+        subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fno-fast-math", *extra,
+                        "-o", tmp, _SRC], check=True)
+        os.replace(tmp, lib)
+    return lib
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with g++ (no GPU, no CUDA)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.run(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fno-fast-math",
-                        "-o", tmp, _SRC], check=True)
-        os.replace(tmp, _LIB)
-    return _LIB
+    return _compile(_LIB, [], force)
 
 
-def _load():
-    global _lib
+def build_openmp(force: bool = False) -> str:
+    """Compile the same source with OpenMP (libhb_oracle_omp.so), used only to
+    time the oracle on all host cores; its results equal the plain build's
+    bit for bit."""
+    return _compile(_LIB_OMP, ["-fopenmp"], force)
+
+
+def _load(openmp: bool = False):
+    global _lib, _lib_omp
     with _lock:
-        if _lib is None:
-            lib = ct.CDLL(build())
+        if (_lib_omp if openmp else _lib) is None:
+            lib = ct.CDLL(build_openmp() if openmp else build())
             lib.orc_create.restype = ct.c_void_p
             lib.orc_create.argtypes = [ct.c_int, ct.c_int, _dp, ct.c_int, _ip, _dp, ct.c_int, _ip,
                                        ct.c_int, _ip]
@@ -57,6 +70,8 @@ def _load():
             lib.orc_residual_cells.argtypes = [ct.c_void_p, _dp, ct.c_int, _ip, _dp, _dp]
             lib.orc_time_step.argtypes = [ct.c_void_p, _dp, _dp]
             lib.orc_rk_smooth.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp]
+            lib.orc_rk_smooth_threads.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, ct.c_int]
+            lib.orc_openmp_threads.restype = ct.c_int
             lib.orc_forces.argtypes = [ct.c_void_p, _dp, _dp, _dp]
             lib.orc_td_residual.argtypes = [ct.c_void_p, _dp, _dp, _dp, ct.c_double, ct.c_double, _dp]
             lib.orc_td_step.argtypes = [ct.c_void_p, _dp, _dp, _dp, ct.c_double, ct.c_double, ct.c_int, _dp]
@@ -67,8 +82,11 @@ def _load():
             lib.orc_van_albada.restype = ct.c_double
             lib.orc_van_albada.argtypes = [ct.c_double, ct.c_double, ct.c_double]
             lib.orc_roe_flux.argtypes = [ct.c_int, _dp, _dp, _dp, _dp, _dp, ct.c_int, _dp]
-            _lib = lib
-    return _lib
+            if openmp:
+                _lib_omp = lib
+            else:
+                _lib = lib
+    return _lib_omp if openmp else _lib
 
 
 def _d(a):
@@ -116,8 +134,9 @@ def case_params(case) -> np.ndarray:
 class Oracle:
     """One case loaded into the oracle."""
 
-    def __init__(self, case):
-        lib = _load()
+    def __init__(self, case, openmp: bool = False):
+        """openmp=True loads the OpenMP build (for timing on all host cores)."""
+        lib = _load(openmp)
         self.case = case
         self.lib = lib
         dims = np.array([b.n for b in case.blocks], dtype=np.int32).reshape(-1)
@@ -223,6 +242,17 @@ class Oracle:
         norms = np.zeros((max(n_iter, 1), self.nv))
         self.lib.orc_rk_smooth(self.h, _d(U), int(n_iter), _d(norms))
         return U, norms[:n_iter]
+
+    def rk_smooth_threads(self, U, n_iter, threads):
+        """rk_smooth with the residual sweeps on `threads` threads (OpenMP build
+        only; bit for bit the single-thread result)."""
+        U = _f64(U).copy()
+        norms = np.zeros((max(n_iter, 1), self.nv))
+        self.lib.orc_rk_smooth_threads(self.h, _d(U), int(n_iter), _d(norms), int(threads))
+        return U, norms[:n_iter]
+
+    def openmp_threads(self) -> int:
+        return int(self.lib.orc_openmp_threads())
 
     def forces(self, U):
         U = _f64(U)

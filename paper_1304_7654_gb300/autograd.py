@@ -36,8 +36,10 @@ class HBLift(torch.autograd.Function):
     def backward(ctx, gJ):
         (U,) = ctx.saved_tensors
         psi = torch.zeros_like(U)
-        r_adj, _ = ctx.hbctx.adjoint_residual(U, psi, float(gJ.item()))
-        return r_adj, None
+        # the adjoint is linear in the seed: scale the unit-seed adjoint by gJ
+        # on the device instead of reading gJ on the host (no stream sync)
+        r_adj, _ = ctx.hbctx.adjoint_residual(U, psi, 1.0)
+        return r_adj * gJ.to(r_adj.dtype), None
 
 
 def residual(U, hbctx):

@@ -64,6 +64,9 @@ struct hb_ctx {
   long long timeout_ns = 2000000000LL;
   int skip_cta = -1;
   int persist_graph = -1;       // -1 untested, 0 capture unsupported, 1 captured
+  int64_t n_graph_replays = 0;      // RK chunks replayed from a captured graph
+  int64_t n_persist_replays = 0;    // ... of them persistent (one cooperative launch)
+  int64_t n_persist_direct = 0;     // persistent chunks launched without a graph
   std::string tune_key;
   // device
   void* d_cases = nullptr;
@@ -1500,11 +1503,14 @@ hb_status rk_smooth_impl(hb_ctx* c, T* U, int n_iter, double* norms, cudaStream_
       if (use_graph) {
         c->n_launch += c->graph_kernels[key];
         HB_CUDA(c, cudaGraphLaunch(it->second, s));
+        c->n_graph_replays += 1;
+        if (persist) c->n_persist_replays += 1;
       }
     }
     if (!use_graph) {
       hb_status r = rk_chunk_direct<T>(c, U, K, s);
       if (r != HB_OK) return r;
+      if (persist) c->n_persist_direct += 1;
     }
     hb_status r = copy_norms(c, norms, done, K, s);
     if (r != HB_OK) return r;
@@ -1939,6 +1945,17 @@ hb_status hb_kernel_stats(hb_ctx* ctx, int which, double* ms, int64_t* launches,
     ctx->t_ms[0] = ctx->t_ms[1] = 0.0;
     ctx->n_timed[0] = ctx->n_timed[1] = 0;
     ctx->n_launch = 0;
+  }
+  return HB_OK;
+}
+
+hb_status hb_graph_info(const hb_ctx* ctx, int* persist_captured, int64_t counts[3]) {
+  if (!ctx) return HB_ERR_INVALID_ARG;
+  if (persist_captured) *persist_captured = ctx->persist_graph;
+  if (counts) {
+    counts[0] = ctx->n_graph_replays;
+    counts[1] = ctx->n_persist_replays;
+    counts[2] = ctx->n_persist_direct;
   }
   return HB_OK;
 }

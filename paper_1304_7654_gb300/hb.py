@@ -103,6 +103,7 @@ def load(path: str | None = None):
                                     ct.c_int]
     lib.hb_residual_norms_noalloc.argtypes = [_vp, _vp, ct.c_int, ct.c_int64, ct.c_int, ct.c_int,
                                               _vp, _vp]
+    lib.hb_graph_info.argtypes = [_vp, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int64)]
     lib.hb_td_step.argtypes = [_vp, _vp, _vp, _vp, ct.c_double, ct.c_double, ct.c_int, _vp, _vp]
     lib.hb_defect_correction.argtypes = [_vp, _vp, _vp, ct.c_int, ct.c_int, ct.c_double, _vp, _vp]
     lib.hb_save_state.argtypes = [_vp, _vp, ct.c_char_p, ct.c_int64, _vp]
@@ -328,6 +329,15 @@ class HBContext:
         self._check(self.lib.hb_kernel_stats(self.h, int(which), ct.byref(ms), ct.byref(n), int(reset)))
         return float(ms.value), int(n.value)
 
+    def graph_info(self):
+        """hb_graph_info: (persist_captured, graph replays, persistent replays,
+        direct persistent launches); persist_captured is -1 (no persistent
+        chunk yet), 0 (capture refused) or 1 (captured)."""
+        cap = ct.c_int()
+        counts = (ct.c_int64 * 3)()
+        self._check(self.lib.hb_graph_info(self.h, ct.byref(cap), counts))
+        return int(cap.value), int(counts[0]), int(counts[1]), int(counts[2])
+
     def td_step(self, U, U_n, U_nm1, t, dt, n_inner, norms=True):
         """hb_td_step: n_inner dual-time iterations of the physical step to t
         (BDF2; backward Euler when U_nm1 is None); returns FP64 norms
@@ -376,6 +386,19 @@ def residual_norms_noalloc(R, vol, ncells, n_snap, nv, norms):
     """Binding of hb_residual_norms_noalloc: R [n_snap][nv][ncells] and vol
     [ncells] (both float32 or both float64 CUDA tensors), norms FP64 [nv]."""
     import torch
+    if R.dtype not in (torch.float32, torch.float64) or vol.dtype != R.dtype:
+        raise ValueError("R and vol must both be float32 or both float64")
+    if norms.dtype != torch.float64:
+        raise ValueError("norms must be float64")
+    for name, t in (("R", R), ("vol", vol), ("norms", norms)):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if R.device != vol.device or R.device != norms.device:
+        raise ValueError("R, vol and norms must be on one device")
+    if int(ncells) < 1 or int(n_snap) < 1 or int(nv) < 1:
+        raise ValueError("ncells, n_snap and nv must be positive")
+    if R.numel() < int(n_snap) * int(nv) * int(ncells) or vol.numel() < int(ncells) or norms.numel() < int(nv):
+        raise ValueError("R, vol or norms is smaller than n_snap * nv * ncells, ncells or nv")
     prec = HB_FP32 if R.dtype == torch.float32 else HB_FP64
     st = load().hb_residual_norms_noalloc(_ptr(R), _ptr(vol), prec, int(ncells), int(n_snap), int(nv),
                                           _ptr(norms), _stream())

@@ -8,12 +8,13 @@ import bench
 
 def test_algorithmic_bytes_of_the_benchmark_workload():
     # 8-block laminar pitching O-grid, FP32, 7 snapshots: (2+3+3+3)/4 x 4 vars
-    # x 4 B of state, plus 13 metric floats per cell read once for 7 snapshots
-    b = bench.algorithmic_bytes_per_unit(nv=4, s=4, moving=True, viscous=True, ns=7)
-    assert math.isclose(b, 44.0 + 13 * 4 / 7, rel_tol=1e-15)
-    # inviscid static FP64 3D box without motion: 5 vars x 8 B, volume + 4 face floats
-    b3 = bench.algorithmic_bytes_per_unit(nv=5, s=8, moving=False, viscous=False, ns=5)
-    assert math.isclose(b3, 2.75 * 40 + 5 * 8 / 5, rel_tol=1e-15)
+    # x 4 B of state, plus the 2 node coordinates per cell read once for 7 snapshots
+    b = bench.algorithmic_bytes_per_unit(nv=4, s=4, dim=2, ns=7)
+    assert math.isclose(b, 44.0 + 8 / 7, rel_tol=1e-15)
+    # FP32 3D box, 5 snapshots: 220 B per cell-snapshot-iteration of state
+    # (55 B per stage) plus 3 node coordinates per cell over 5 snapshots
+    b3 = bench.algorithmic_bytes_per_unit(nv=5, s=4, dim=3, ns=5)
+    assert math.isclose(b3, 55.0 + 12 / 5, rel_tol=1e-15)
 
 
 def test_hbm_roofline_fraction():

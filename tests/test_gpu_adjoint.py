@@ -86,8 +86,17 @@ def test_adjoint_matches_oracle_dual_columns(name):
 
 def test_adjoint_full_size_central_differences_32_cells():
     """4 blocks, 512 x 256 cells, N_H = 4, laminar, pitching: the adjoint of
-    psi . R + J_seed J at 32 seeded cells x 4 variables x 9 snapshots against
-    central differences of the GPU FP64 primal with step 1e-7 * max(1,|U|)."""
+    psi . R + J_seed J at 32 seeded cells x 4 variables x 9 snapshots (1,152
+    columns) against plain central differences of the GPU FP64 primal with
+    step h = 1e-7 * max(1, |U|), column by column:
+    |adjoint - fd| <= 1e-6 * max(|fd|, s), where s = (sum_e |psi_e (R+_e -
+    R-_e)| + |J_seed (J+ - J-)|) / 2h is the column's own scale (the size of
+    the terms its entries cancel).  A column whose plain difference carries
+    more truncation error than that (stiff limiter) must meet the same bound
+    against the Richardson-extrapolated difference, and its plain difference
+    must be off by no more than its own estimated truncation error; at least
+    95 % of the columns meet the plain bound.  Every column is also compared
+    with the oracle's exact (dual-number) column."""
     cs = _with_incidence(C.adjoint_ogrid4())
     o = Oracle(cs)
     U = o.init_state(C.noise(cs), 0.01)
@@ -99,40 +108,54 @@ def test_adjoint_full_size_central_differences_32_cells():
     r_adj, _ = ctx.adjoint_residual(Ug, psi, J_seed)
     cells = C.sample_cells(cs, 32, 11)
     cols = np.array([[*c, v, n] for c in cells for v in range(cs.nv) for n in range(cs.n_snap)], dtype=np.int32)
+    assert len(cols) == 1152
     got = _gather(ctx, r_adj.cpu().numpy(), cols)
-    fd = np.zeros(len(cols))
-    R = ctx.new_state()
+    fd, fd_rich, scale = np.zeros(len(cols)), np.zeros(len(cols)), np.zeros(len(cols))
+    Rm = ctx.new_state()
 
     def central(a, u0, h):
         Ug[a] = u0 + h
         Rp = ctx.residual(Ug).clone()
         _, Jp = ctx.forces(Ug)
         Ug[a] = u0 - h
-        Rm = ctx.residual(Ug, R)
+        ctx.residual(Ug, Rm)
         _, Jm = ctx.forces(Ug)
         Ug[a] = u0
-        return (torch.dot(psi, Rp - Rm).item() + J_seed * (Jp - Jm).item()) / (2 * h)
+        dR = psi * (Rp - Rm)
+        dJ = J_seed * (Jp - Jm).item()
+        return (dR.sum().item() + dJ) / (2 * h), (dR.abs().sum().item() + abs(dJ)) / (2 * h)
 
     for q, (b, i, j, k, v, n) in enumerate(cols):
         off, st, _ = ctx.layouts[b]
         a = off + n * st[0] + v * st[1] + (j + 2) * st[3] + (i + 2)
         u0 = Ug[a].item()
         h = 1e-7 * max(1.0, abs(u0))
-        # Richardson-extrapolated central difference (truncation O(h^4)): the
-        # limiter is strongly curved where neighbour differences are small
-        fd[q] = (4.0 * central(a, u0, 0.5 * h) - central(a, u0, h)) / 3.0
-    # relative error over the checked columns (2-norm); a column whose
-    # central difference carries limiter curvature (small neighbour
-    # differences) is bounded per column at 1e-5 of the largest entry
-    rel2 = np.linalg.norm(got - fd) / np.linalg.norm(got)
-    err = np.abs(got - fd)
+        fd[q], scale[q] = central(a, u0, h)
+        # extra: Richardson-extrapolated central difference (truncation O(h^4))
+        fd_rich[q] = (4.0 * central(a, u0, 0.5 * h)[0] - fd[q]) / 3.0
+    norm = np.maximum(np.abs(fd), scale)
+    rel = np.abs(got - fd) / norm
+    rel_rich = np.abs(got - fd_rich) / np.maximum(np.abs(fd_rich), scale)
+    # the plain difference's own truncation error, estimated from the
+    # half-step difference: where the van Albada limiter is stiff (two
+    # neighbour values within ~1e-5 of each other) it exceeds 1e-6 of the
+    # column at h = 1e-7, and there the O(h^4) Richardson value must agree
+    trunc = np.abs(fd - fd_rich)
+    plain_ok = rel < 1e-6
+    stiff_ok = (rel_rich < 1e-6) & (np.abs(got - fd) <= 1.5 * trunc + 1e-6 * norm)
+    print(f"adjoint vs plain central differences (h = 1e-7): {plain_ok.sum()} of {len(cols)} columns within "
+          f"1e-6 (worst {rel.max():.2e}, median {np.median(rel):.2e}); the others within 1e-6 of the "
+          f"Richardson value (worst {rel_rich[~plain_ok].max() if (~plain_ok).any() else 0.0:.2e}) and within "
+          f"the plain difference's own truncation error")
+    bad = ~(plain_ok | stiff_ok)
+    q = int(np.argmax(np.where(bad, rel, 0.0)))
+    assert not bad.any(), (int(bad.sum()), cols[q], got[q], fd[q], fd_rich[q], scale[q])
+    assert plain_ok.mean() >= 0.95, plain_ok.mean()
+    # every column against the oracle's exact dual-number column
+    ref = o.adjoint_columns(U, _psi_oracle(o, ctx, psi), J_seed, cols)
+    err = np.abs(got - ref)
     q = int(np.argmax(err))
-    assert rel2 < 1e-6, (rel2, cols[q], got[q], fd[q])
-    assert err.max() < 1e-5 * np.abs(got).max(), (err.max(), cols[q], got[q], fd[q])
-    # and against the oracle's exact columns on a subset
-    sub = cols[:: 8]
-    ref = o.adjoint_columns(U, _psi_oracle(o, ctx, psi), J_seed, sub)
-    assert np.abs(_gather(ctx, r_adj.cpu().numpy(), sub) - ref).max() < 1e-10 * np.abs(ref).max()
+    assert err.max() < 1e-10 * np.abs(ref).max(), (err.max(), cols[q], got[q], ref[q])
 
 
 def _psi_oracle(o, ctx, psi):
@@ -168,9 +191,9 @@ def test_dot_product_and_autograd():
     (gU,) = torch.autograd.grad((Rt * psi).sum(), Ua)
     assert torch.equal(gU, r_adj)
     Jt = hbag.lift(Ua, ctx)
-    (gJ,) = torch.autograd.grad(2.0 * Jt, Ua)
-    r2, _ = ctx.adjoint_residual(Ug, torch.zeros_like(psi), 2.0)
-    assert torch.equal(gJ, r2)
+    (gJ,) = torch.autograd.grad(0.7 * Jt, Ua)
+    r2, _ = ctx.adjoint_residual(Ug, torch.zeros_like(psi), 0.7)
+    assert torch.allclose(gJ, r2, rtol=1e-13, atol=1e-13 * r2.abs().max().item())
 
 
 def test_adjoint_is_bitwise_deterministic():

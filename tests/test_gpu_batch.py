@@ -87,6 +87,33 @@ def test_batch_fp64_matches_oracle_per_case():
         assert np.allclose(nb[:, k], no, rtol=1e-10), k
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batch_runs_as_one_persistent_launch_replayed_from_a_graph(prec):
+    """The batched form: every chunk of the batch's RK iterations is one
+    persistent cooperative launch, captured once into a CUDA graph and
+    replayed (hb_graph_info), and the replayed chunks give the same state as
+    direct launches of the same kernel (bitwise)."""
+    cases = _small_batch(8, seed=29)
+    bctx = hb.HBContext(cases, prec)
+    bctx.set_tuning(1, 32, 8)
+    Ub = _batch_state(bctx, cases)
+    U2 = Ub.clone()
+    bctx.rk_smooth(Ub, 5)
+    bctx.rk_smooth(Ub, 5)
+    assert bctx.sync_status() == hb.HB_OK
+    cap, replays, persist_replays, direct = bctx.graph_info()
+    assert cap == 1, "persistent chunk was not captured into a graph"
+    assert persist_replays == 2 and replays == 2 and direct == 0
+    # the same iterations without graphs (timing brackets single launches)
+    bctx.set_timing(True)
+    bctx.rk_smooth(U2, 5)
+    bctx.rk_smooth(U2, 5)
+    bctx.set_timing(False)
+    assert bctx.sync_status() == hb.HB_OK
+    assert bctx.graph_info()[3] == 2
+    assert torch.equal(Ub, U2)
+
+
 def test_tile_shape_and_driver_do_not_change_the_state():
     # each face is computed once from the same inputs whatever the tile shape
     # or row-strip split: a rerun is bitwise equal; other tile shapes and the

@@ -172,6 +172,13 @@ def test_full_size_ns_ogrid8_sampled_residual(prec):
         ni, nj, _ = blk.n
         for (i, j) in [(0, 0), (ni - 1, 0), (0, nj - 1), (ni - 1, nj - 1), (1, 1), (ni // 2, 0)]:
             cells.append([b, i, j, 0])
+    # the sharp trailing edge: the wall cells on both sides of it (blocks 0
+    # and 3 meet there across the periodic wrap cut)
+    n3 = cs.blocks[3].n[0]
+    for j in (0, 1):
+        for i in (0, 1, 2):
+            cells.append([0, i, j, 0])
+            cells.append([3, n3 - 1 - i, j, 0])
     cells = np.array(cells, dtype=np.int32)
     Rref, sc = o.residual_cells(U, cells)
     R = ctx.residual(Ug).double().cpu().numpy()
@@ -182,17 +189,10 @@ def test_full_size_ns_ogrid8_sampled_residual(prec):
             for v in range(cs.nv):
                 got[q, n, v] = R[off + n * st[0] + v * st[1] + (j + 2) * st[3] + (i + 2)]
     err = np.abs(got - Rref) / sc
-    # cells at the sharp trailing edge (global i within 2 of the edge, j <= 1)
-    # use ghost cells that the point reflection inverts (|V| ~ 7e-9); there
-    # FP32 rounding of temperature differences is amplified by |S|/|V|:
-    # measured up to 1.4e-4 (hardware reciprocal forms), bounded by 2e-4.
-    # Every other cell meets TOL.
-    n3 = cs.blocks[3].n[0]
-    te = np.array([j <= 1 and ((b == 0 and i <= 2) or (b == 3 and i >= n3 - 3)) for (b, i, j, k) in cells])
-    e_other = err[~te]
-    q, n, v = np.unravel_index(np.argmax(e_other), e_other.shape)
-    assert e_other.max() < TOL[prec], (e_other.max(), tuple(cells[~te][q]), n, v)
-    assert err[te].max() < (TOL[prec] if prec == "fp64" else 2e-4), err[te].max()
+    q, n, v = np.unravel_index(np.argmax(err), err.shape)
+    print(f"full-size ns_ogrid8 {prec}: max {err.max():.2e}, median {np.median(err):.2e}, "
+          f"per variable {[float(f'{x:.2e}') for x in err.max(axis=(0, 1))]}")
+    assert err.max() < TOL[prec], (err.max(), tuple(cells[q]), n, v)
 
 
 def test_full_size_ns_ogrid8_stays_finite_over_600_iterations():
