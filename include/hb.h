@@ -86,7 +86,12 @@ typedef struct {
  * directions q < p it may extend over ghost cells (block corners), along
  * q > p it must stay inside the block.  Sources must be interior cells, or
  * ghost cells along directions q < p.  This is the device form of the
- * paper's per-RK-step cut exchange (Sec. 3.1). */
+ * paper's per-RK-step cut exchange (Sec. 3.1).  src_blk = HB_EXTERNAL_BLOCK
+ * marks a box whose source block lives in another process (a block
+ * decomposition over several GPUs, the paper's MPI distribution of blocks,
+ * Sec. 2-3): the library never writes it; the caller fills it between the
+ * halo passes (hb_halo_pass, hb_pack_halo / hb_unpack_halo). */
+#define HB_EXTERNAL_BLOCK (-1)
 typedef struct {
   int dst_blk, src_blk;
   int lo[3], hi[3];
@@ -191,6 +196,50 @@ hb_status hb_residual(hb_ctx* ctx, const void* U, void* R, void* stream);
  * and the launch returns); chunks are captured and replayed as CUDA graphs
  * where stream capture is available. */
 hb_status hb_rk_smooth(hb_ctx* ctx, void* U, int n_iter, double* norms_dev, void* stream);
+
+/* Block decomposition over processes (the paper's distribution of blocks
+ * over MPI ranks with one aggregated cut exchange per RK step, Sec. 2-3).
+ * A context whose cuts include HB_EXTERNAL_BLOCK boxes is one process's
+ * share of a multi-block case; hb_rk_smooth and hb_autotune refuse it
+ * (HB_ERR_UNSUPPORTED) and the caller advances it stage by stage:
+ *   for each RK stage s = 0..3 and its input Uin:
+ *     for each pass p (direction) = 0..dim-1:
+ *       hb_pack_halo   -- the sources of the other processes' pass-p boxes
+ *       (send / receive the packed buffers)
+ *       hb_halo_pass(p)  -- this context's own cuts and boundary ghosts
+ *       hb_unpack_halo -- the received pass-p boxes
+ *     hb_rk_stage(Uin, U0, Uout, s)
+ * so that corners see the same values as on one GPU.  hb_residual and
+ * hb_forces fill only the context's own ghosts: the external boxes of their
+ * U must have been filled by the caller.  The adjoint is not available on
+ * such contexts (HB_ERR_UNSUPPORTED). */
+
+/* The cut copies and physical-boundary ghosts of one pass (direction `pass`,
+ * 0 .. dim-1) in place on U, external boxes untouched.  Asynchronous.
+ * Errors: HB_ERR_INVALID_ARG (null U, pass out of range). */
+hb_status hb_halo_pass(hb_ctx* ctx, void* U, int pass, void* stream);
+
+/* One Runge-Kutta stage (coefficients 1/4, 1/3, 1/2, 1 for stage 0..3) with
+ * local time steps from U0: Uout = U0 - alpha_stage dtau/V R_HB(Uin) on
+ * interior cells (Uout's ghosts untouched); every ghost of Uin must be
+ * filled.  norm_sums (device FP64 [n_cases][nv], may be NULL) receives at
+ * stage 0 the fixed-order sums over the context's interior cells and
+ * snapshots of (R/V)^2 per variable, the terms of the RMS norms of
+ * hb_rk_smooth, so that processes can add theirs before the square root.
+ * Uout may be U0 (each cell reads its own U0 entries before writing them)
+ * but not Uin.  2D contexts.  Errors: HB_ERR_INVALID_ARG (null pointers,
+ * stage out of range, Uout aliasing Uin), HB_ERR_UNSUPPORTED (3D).
+ * Asynchronous. */
+hb_status hb_rk_stage(hb_ctx* ctx, const void* Uin, const void* U0, void* Uout, int stage, double* norm_sums,
+                      void* stream);
+
+/* Staging buffers of the halo exchange: buf[e] = U[idx[e]] (pack) or
+ * U[idx[e]] = buf[e] (unpack) for e < n.  idx: device int64 state offsets
+ * (hb_state_layout); buf: device array of n elements of the context's
+ * precision; both caller-owned.  n = 0 does nothing.  Errors:
+ * HB_ERR_INVALID_ARG (n < 0, null pointers with n > 0).  Asynchronous. */
+hb_status hb_pack_halo(hb_ctx* ctx, const void* U, const int64_t* idx, int64_t n, void* buf, void* stream);
+hb_status hb_unpack_halo(hb_ctx* ctx, void* U, const int64_t* idx, int64_t n, const void* buf, void* stream);
 
 /* Force coefficients of every body at every snapshot, packed
  * [snapshot][body][cl, cd, cm] in FP64 (cm is zero unless functag == 3), as

@@ -525,10 +525,21 @@ BFace bface(const Block& B, int p, int side, const int* t) {
 }
 
 template <class S>
+void fill_pass(const Case& C, S* U, int pass);
+
+template <class S>
 void fill_ghosts(const Case& C, S* U) {
-  for (int pass = 0; pass < C.dim; ++pass) {
+  for (int pass = 0; pass < C.dim; ++pass) fill_pass(C, U, pass);
+}
+
+// the cut copies, then the boundary ghosts, of one pass; a cut whose source
+// block is -1 lies in another process's share of a block decomposition and
+// is left for the exchange to fill
+template <class S>
+void fill_pass(const Case& C, S* U, int pass) {
+  {
     for (const Cut& ct : C.cuts) {
-      if (ct.pass != pass) continue;
+      if (ct.pass != pass || ct.src < 0) continue;
       const Block& D = C.B[ct.dst];
       const Block& Sb = C.B[ct.src];
       for (int k = ct.lo[2]; k < ct.hi[2]; ++k)
@@ -962,6 +973,34 @@ void rk_smooth(Case* C, double* U, int n_iter, double* norms, int threads) {
 
 void orc_rk_smooth(void* h, double* U, int n_iter, double* norms) {
   rk_smooth((Case*)h, U, n_iter, norms, 1);
+}
+
+// one pass of the ghost fill in place (cuts with source block -1 skipped)
+void orc_halo_pass(void* h, double* U, int pass) { fill_pass(*(Case*)h, U, pass); }
+
+// one stage of the smoother above, out of place and without refilling the
+// ghosts of Uin: Uout = U0 - alpha_stage dt(U0)/V R(Uin) on interior cells;
+// at stage 0 sums[v] = sum over interior cells and snapshots of (R/V)^2
+void orc_rk_stage(void* h, const double* Uin, const double* U0, double* Uout, int stage, double* sums) {
+  Case* C = (Case*)h;
+  const double alpha[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
+  std::vector<double> R(C->total);
+  residual_sweep(*C, Uin, R.data(), 1);
+  double acc[5] = {0, 0, 0, 0, 0};
+  for_interior(*C, [&](int b, int i, int j, int k) {
+    int64_t c = C->B[b].cell(i, j, k);
+    double V = C->B[b].vol[c];
+    for (int n = 0; n < C->ns; ++n) {
+      double t = local_dt(*C, U0, b, i, j, k, n);
+      for (int v = 0; v < C->nv; ++v) {
+        int64_t a = C->at(b, n, v, c);
+        if (stage == 0) acc[v] += (R[a] / V) * (R[a] / V);
+        Uout[a] = U0[a] - alpha[stage] * t / V * R[a];
+      }
+    }
+  });
+  if (stage == 0 && sums)
+    for (int v = 0; v < C->nv; ++v) sums[v] = acc[v];
 }
 
 // the same iterations with the residual sweeps on `threads` threads (only in

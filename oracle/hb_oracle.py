@@ -71,6 +71,8 @@ def _load(openmp: bool = False):
             lib.orc_time_step.argtypes = [ct.c_void_p, _dp, _dp]
             lib.orc_rk_smooth.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp]
             lib.orc_rk_smooth_threads.argtypes = [ct.c_void_p, _dp, ct.c_int, _dp, ct.c_int]
+            lib.orc_halo_pass.argtypes = [ct.c_void_p, _dp, ct.c_int]
+            lib.orc_rk_stage.argtypes = [ct.c_void_p, _dp, _dp, _dp, ct.c_int, _dp]
             lib.orc_openmp_threads.restype = ct.c_int
             lib.orc_forces.argtypes = [ct.c_void_p, _dp, _dp, _dp]
             lib.orc_td_residual.argtypes = [ct.c_void_p, _dp, _dp, _dp, ct.c_double, ct.c_double, _dp]
@@ -250,6 +252,20 @@ class Oracle:
         norms = np.zeros((max(n_iter, 1), self.nv))
         self.lib.orc_rk_smooth_threads(self.h, _d(U), int(n_iter), _d(norms), int(threads))
         return U, norms[:n_iter]
+
+    def halo_pass(self, U, p):
+        """One pass of the ghost fill in place on U (float64 array of the
+        oracle layout); cuts with source block -1 are left alone."""
+        assert U.dtype == np.float64 and U.flags.c_contiguous and U.size == self.size
+        self.lib.orc_halo_pass(self.h, _d(U), int(p))
+
+    def rk_stage(self, Uin, U0, Uout, stage, sums=None):
+        """One RK stage out of place, Uin's ghosts as given; at stage 0 the
+        sums of (R/V)^2 per variable into sums (nv doubles) if given."""
+        for a in (Uin, U0, Uout):
+            assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == self.size
+        self.lib.orc_rk_stage(self.h, _d(Uin), _d(U0), _d(Uout), int(stage),
+                              _d(sums) if sums is not None else None)
 
     def openmp_threads(self) -> int:
         return int(self.lib.orc_openmp_threads())

@@ -81,6 +81,7 @@ struct hb_ctx {
   // fused ghost fill (2D): every ghost cell as a chain of boundary maps of one
   // interior root cell, grouped by the tile that owns the root
   bool jobs_ok = false;          // ghost jobs resolved (2D contexts)
+  int64_t external_cells = 0;    // ghost cells of external cuts (filled by the caller: block decomposition)
   bool halo_phases = false;      // tuning: run the halo passes between stages instead
   bool fused() const { return jobs_ok && !halo_phases; }
   struct GhostJobHost { int root_blk, root_i, root_j; hbk::GhostJob job; };
@@ -345,10 +346,11 @@ hb_status build_tables(hb_ctx* ctx, const CaseHost& ch, Tables& T) {
   };
   for (int q = 0; q < d.n_cuts; ++q) {
     const hb_cut_desc& c = d.cuts[q];
-    if (c.dst_blk < 0 || c.dst_blk >= nb || c.src_blk < 0 || c.src_blk >= nb)
+    const bool external = c.src_blk == HB_EXTERNAL_BLOCK;
+    if (c.dst_blk < 0 || c.dst_blk >= nb || (!external && (c.src_blk < 0 || c.src_blk >= nb)))
       return fail(ctx, HB_ERR_INVALID_ARG, "cut " + std::to_string(q) + ": block id out of range");
     const BlockDev& D = blk(c.dst_blk);
-    const BlockDev& S = blk(c.src_blk);
+    const BlockDev& S = blk(external ? c.dst_blk : c.src_blk);
     int p = -1;
     for (int a = 0; a < dim; ++a)
       if (c.lo[a] < 0 || c.hi[a] > D.n[a]) p = a;
@@ -371,6 +373,13 @@ hb_status build_tables(hb_ctx* ctx, const CaseHost& ch, Tables& T) {
           if (dim == 2) sc[2] = 0;
           if (!ghost_ok(D, p, dc))
             return fail(ctx, HB_ERR_INVALID_ARG, "cut " + std::to_string(q) + ": destination outside the ghost layers of its pass");
+          if (external) {   // filled by the caller between halo passes: only coverage is recorded
+            const int64_t dcell = pcell(D, dc[0], dc[1], dc[2]);
+            if (cover[c.dst_blk][dcell]++)
+              return fail(ctx, HB_ERR_INVALID_ARG, "cut " + std::to_string(q) + ": ghost cell filled twice");
+            ctx->external_cells++;
+            continue;
+          }
           if (!src_ok(S, p, sc))
             return fail(ctx, HB_ERR_INVALID_ARG, "cut " + std::to_string(q) + ": source not interior or earlier-pass ghost");
           const int64_t dcell = pcell(D, dc[0], dc[1], dc[2]);
@@ -994,7 +1003,7 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
       CK(cudaMemcpy(ctx->d_bc[p], Tb.bc[p].data(), sizeof(BcRec) * ctx->nbc[p], cudaMemcpyHostToDevice));
     }
   }
-  if (ctx->dim == 2) {
+  if (ctx->dim == 2 && ctx->external_cells == 0) {
     int bc_index[3] = {0, 0, 0};
     std::vector<BcRec> all;
     for (int p = 0; p < 3; ++p) {
@@ -1087,7 +1096,7 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
   CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
   CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
   // adjoint tables (FP64, 2D, single case)
-  if (ctx->prec == HB_FP64 && ctx->dim == 2 && ctx->cases.size() == 1) {
+  if (ctx->prec == HB_FP64 && ctx->dim == 2 && ctx->cases.size() == 1 && ctx->external_cells == 0) {
     const int nb = (int)ctx->blocks.size();
     std::vector<int64_t> foff(nb + 1, 0), coff(nb + 1, 0);
     for (int b = 0; b < nb; ++b) {
@@ -1296,6 +1305,52 @@ hb_status rk_iteration(hb_ctx* c, T* U, double* norm_out, cudaStream_t s, const 
       }
     }
   }
+  return HB_OK;
+}
+
+// the cut copies and boundary ghosts of one pass (direction), in place
+template <typename T>
+hb_status halo_pass(hb_ctx* c, T* U, int pass, cudaStream_t s) {
+  hbk::HaloParams<T> p;
+  p.cases = (const CaseDev<T>*)c->d_cases;
+  p.blocks = c->d_blocks;
+  p.g = geo_of<T>(c);
+  p.U = U;
+  p.ns_max = c->ns_max;
+  p.copies = c->d_copy[pass];
+  p.ncopy = c->ncopy[pass];
+  p.bcs = c->d_bc[pass];
+  p.nbc = c->nbc[pass];
+  if ((int64_t)(p.ncopy + p.nbc) == 0) return HB_OK;
+  TimedScope ts(c, 1, s);
+  if (c->dim == 3) HB_CUDA(c, hbk::launch_halo3d<T>(p, s));
+  else HB_CUDA(c, hbk::launch_halo<T>(p, s));
+  return HB_OK;
+}
+
+// one RK stage Uout = U0 - alpha_stage dtau/V R(Uin), the halos of Uin filled
+// by the caller; at stage 0 the per-case sums of (R/V)^2 into sums[case][nv]
+template <typename T>
+hb_status rk_stage_impl(hb_ctx* c, const T* Uin, const T* U0, T* Uout, int stage, double* sums, cudaStream_t s) {
+  static const double alpha[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
+  auto p = stage_params<T>(c);
+  p.Uprev = Uin;
+  p.U0 = U0;
+  p.Unext = Uout;
+  p.alpha = (T)alpha[stage];
+  p.partials = (stage == 0 && sums) ? c->d_partials : nullptr;
+  hb_status r = hb_source<T>(c, Uin, s);
+  if (r != HB_OK) return r;
+  if (c->large_ns()) p.H = (const T*)c->d_H;
+  r = stage_all<T>(c, p, 1, s);
+  if (r != HB_OK) return r;
+  if (p.partials)
+    for (size_t k = 0; k < c->cases.size(); ++k) {
+      const CaseHost& ch = c->cases[k];
+      c->n_launch++;
+      HB_CUDA(c, hbk::launch_norm_finish(c->d_partials + (size_t)8 * ch.tile0, ch.ntiles, c->nv, 1.0,
+                                         sums + (size_t)c->nv * k, c->d_err, s, 1));
+    }
   return HB_OK;
 }
 
@@ -1808,6 +1863,38 @@ hb_status hb_init_state(hb_ctx* ctx, void* U, const double* noise, double amp, v
                               : init_impl<double>(ctx, (double*)U, noise, amp, s);
 }
 
+hb_status hb_halo_pass(hb_ctx* ctx, void* U, int pass, void* stream) {
+  if (!ctx || !U || pass < 0 || pass >= ctx->dim) return fail(ctx, HB_ERR_INVALID_ARG, "bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  return ctx->prec == HB_FP32 ? halo_pass<float>(ctx, (float*)U, pass, s) : halo_pass<double>(ctx, (double*)U, pass, s);
+}
+
+hb_status hb_rk_stage(hb_ctx* ctx, const void* Uin, const void* U0, void* Uout, int stage, double* norm_sums,
+                      void* stream) {
+  if (!ctx || !Uin || !U0 || !Uout || stage < 0 || stage > 3) return fail(ctx, HB_ERR_INVALID_ARG, "bad argument");
+  if (Uin == Uout) return fail(ctx, HB_ERR_INVALID_ARG, "Uout must not alias Uin");
+  if (ctx->dim != 2) return fail(ctx, HB_ERR_UNSUPPORTED, "hb_rk_stage: 2D contexts");
+  cudaStream_t s = (cudaStream_t)stream;
+  return ctx->prec == HB_FP32
+             ? rk_stage_impl<float>(ctx, (const float*)Uin, (const float*)U0, (float*)Uout, stage, norm_sums, s)
+             : rk_stage_impl<double>(ctx, (const double*)Uin, (const double*)U0, (double*)Uout, stage, norm_sums, s);
+}
+
+hb_status hb_pack_halo(hb_ctx* ctx, const void* U, const int64_t* idx, int64_t n, void* buf, void* stream) {
+  if (!ctx || n < 0 || (n > 0 && (!U || !idx || !buf))) return fail(ctx, HB_ERR_INVALID_ARG, "bad argument");
+  ctx->n_launch += n > 0;
+  HB_CUDA(ctx, hbk::launch_halo_pack(U, idx, n, buf, ctx->prec == HB_FP32, false, (cudaStream_t)stream));
+  return HB_OK;
+}
+
+hb_status hb_unpack_halo(hb_ctx* ctx, void* U, const int64_t* idx, int64_t n, const void* buf, void* stream) {
+  if (!ctx || n < 0 || (n > 0 && (!U || !idx || !buf))) return fail(ctx, HB_ERR_INVALID_ARG, "bad argument");
+  ctx->n_launch += n > 0;
+  HB_CUDA(ctx, hbk::launch_halo_pack(U, idx, n, const_cast<void*>(buf), ctx->prec == HB_FP32, true,
+                                     (cudaStream_t)stream));
+  return HB_OK;
+}
+
 hb_status hb_exchange_halos(hb_ctx* ctx, void* U, void* stream) {
   if (!ctx || !U) return fail(ctx, HB_ERR_INVALID_ARG, "null argument");
   cudaStream_t s = (cudaStream_t)stream;
@@ -1824,6 +1911,8 @@ hb_status hb_residual(hb_ctx* ctx, const void* U, void* R, void* stream) {
 
 hb_status hb_rk_smooth(hb_ctx* ctx, void* U, int n_iter, double* norms, void* stream) {
   if (!ctx || !U || n_iter < 0) return fail(ctx, HB_ERR_INVALID_ARG, "bad argument");
+  if (ctx->external_cells)
+    return fail(ctx, HB_ERR_UNSUPPORTED, "external cuts: advance with hb_halo_pass / hb_rk_stage and the caller's exchange");
   if (n_iter == 0) return HB_OK;
   cudaStream_t s = (cudaStream_t)stream;
   return ctx->prec == HB_FP32 ? rk_smooth_impl<float>(ctx, (float*)U, n_iter, norms, s)
@@ -1889,6 +1978,7 @@ hb_status hb_adjoint_residual(hb_ctx* ctx, const void* U, const void* psi, doubl
 hb_status hb_autotune(hb_ctx* ctx, const void* U, int iters, void* stream) {
   if (!ctx || !U || iters < 1) return fail(ctx, HB_ERR_INVALID_ARG, "bad argument");
   if (ctx->dim == 3) return HB_OK;   // one 3D tile shape and driver: nothing to choose
+  if (ctx->external_cells) return fail(ctx, HB_ERR_UNSUPPORTED, "external cuts: the autotuner times hb_rk_smooth");
   cudaStream_t s = (cudaStream_t)stream;
   return ctx->prec == HB_FP32 ? autotune_impl<float>(ctx, (const float*)U, iters, s)
                               : autotune_impl<double>(ctx, (const double*)U, iters, s);

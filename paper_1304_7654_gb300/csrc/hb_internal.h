@@ -211,8 +211,13 @@ cudaError_t launch_persist(const PersistParams<T>& p, int viscous, int TI, int T
 template <typename T>
 bool persist_available(int TI, int TJ);
 
+// raw = 1: out = the fixed-order sum itself (no scaling, no square root)
 cudaError_t launch_norm_finish(const double* partials, int ntiles, int nv, double inv_count,
-                               double* out, int* err, cudaStream_t s);
+                               double* out, int* err, cudaStream_t s, int raw = 0);
+// gather (unpack = false: buf[e] = U[idx[e]]) or scatter (U[idx[e]] = buf[e])
+// of state elements for the halo exchange of a block decomposition
+cudaError_t launch_halo_pack(const void* U, const int64_t* idx, int64_t n, void* buf, bool fp32, bool unpack,
+                             cudaStream_t s);
 // defect correction, elementwise over n state entries: u32 = (float) u64;
 // src = (float)(sigma r64 - r32); u64 += (v32 - u32) / sigma (in FP64)
 cudaError_t launch_cast_down(const double* u64, float* u32, int64_t n, cudaStream_t s);

@@ -9,7 +9,7 @@ namespace hbk {
 // fixed-order FP64 finish of the per-tile norm partials: thread q < nv walks
 // the tiles in order; the result is the RMS over cells and snapshots
 __global__ void norm_finish_kernel(const double* partials, int ntiles, int nv, double inv_count,
-                                   double* out, int* err) {
+                                   double* out, int* err, int raw) {
   __shared__ double acc[8][33];
   const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
   if (q < nv) {
@@ -21,15 +21,45 @@ __global__ void norm_finish_kernel(const double* partials, int ntiles, int nv, d
   if (threadIdx.x < nv) {
     double s = 0.0;
     for (int l = 0; l < 32; ++l) s += acc[threadIdx.x][l];
-    double r = sqrt(s * inv_count);
+    double r = raw ? s : sqrt(s * inv_count);
     if (out) out[threadIdx.x] = r;
     if (!(r == r) || r > 1.0e300) atomicExch(err, 4);
   }
 }
 
 cudaError_t launch_norm_finish(const double* partials, int ntiles, int nv, double inv_count,
-                               double* out, int* err, cudaStream_t s) {
-  norm_finish_kernel<<<1, 256, 0, s>>>(partials, ntiles, nv, inv_count, out, err);
+                               double* out, int* err, cudaStream_t s, int raw) {
+  norm_finish_kernel<<<1, 256, 0, s>>>(partials, ntiles, nv, inv_count, out, err, raw);
+  return cudaGetLastError();
+}
+
+// halo staging buffers of a block decomposition: buf[e] = U[idx[e]] (pack)
+// and U[idx[e]] = buf[e] (unpack), e < n; idx are state offsets
+template <typename T>
+__global__ void halo_pack_kernel(const T* __restrict__ U, const int64_t* __restrict__ idx, int64_t n,
+                                 T* __restrict__ buf) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    buf[e] = U[idx[e]];
+}
+template <typename T>
+__global__ void halo_unpack_kernel(T* __restrict__ U, const int64_t* __restrict__ idx, int64_t n,
+                                   const T* __restrict__ buf) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    U[idx[e]] = buf[e];
+}
+
+cudaError_t launch_halo_pack(const void* U, const int64_t* idx, int64_t n, void* buf, bool fp32, bool unpack,
+                             cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t want = (n + 255) / 256;
+  const unsigned grid = (unsigned)(want < 4096 ? want : 4096);
+  if (fp32) {
+    if (unpack) halo_unpack_kernel<float><<<grid, 256, 0, s>>>((float*)U, idx, n, (const float*)buf);
+    else halo_pack_kernel<float><<<grid, 256, 0, s>>>((const float*)U, idx, n, (float*)buf);
+  } else {
+    if (unpack) halo_unpack_kernel<double><<<grid, 256, 0, s>>>((double*)U, idx, n, (const double*)buf);
+    else halo_pack_kernel<double><<<grid, 256, 0, s>>>((const double*)U, idx, n, (double*)buf);
+  }
   return cudaGetLastError();
 }
 

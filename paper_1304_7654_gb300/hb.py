@@ -104,6 +104,10 @@ def load(path: str | None = None):
     lib.hb_residual_norms_noalloc.argtypes = [_vp, _vp, ct.c_int, ct.c_int64, ct.c_int, ct.c_int,
                                               _vp, _vp]
     lib.hb_graph_info.argtypes = [_vp, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int64)]
+    lib.hb_halo_pass.argtypes = [_vp, _vp, ct.c_int, _vp]
+    lib.hb_rk_stage.argtypes = [_vp, _vp, _vp, _vp, ct.c_int, _vp, _vp]
+    lib.hb_pack_halo.argtypes = [_vp, _vp, _vp, ct.c_int64, _vp, _vp]
+    lib.hb_unpack_halo.argtypes = [_vp, _vp, _vp, ct.c_int64, _vp, _vp]
     lib.hb_td_step.argtypes = [_vp, _vp, _vp, _vp, ct.c_double, ct.c_double, ct.c_int, _vp, _vp]
     lib.hb_defect_correction.argtypes = [_vp, _vp, _vp, ct.c_int, ct.c_int, ct.c_double, _vp, _vp]
     lib.hb_save_state.argtypes = [_vp, _vp, ct.c_char_p, ct.c_int64, _vp]
@@ -328,6 +332,27 @@ class HBContext:
         ms, n = ct.c_double(), ct.c_int64()
         self._check(self.lib.hb_kernel_stats(self.h, int(which), ct.byref(ms), ct.byref(n), int(reset)))
         return float(ms.value), int(n.value)
+
+    # ---- block decomposition (a share of a multi-block case with external boxes)
+    def halo_pass(self, U, p):
+        """hb_halo_pass: this context's cuts and boundary ghosts of pass p."""
+        self._check(self.lib.hb_halo_pass(self.h, _ptr(U), int(p), _stream()))
+
+    def rk_stage(self, Uin, U0, Uout, stage, sums=None):
+        """hb_rk_stage: Uout = U0 - alpha dtau/V R(Uin); at stage 0 the FP64
+        sums of (R/V)^2 per case and variable into sums ([n_cases][nv])."""
+        self._check(self.lib.hb_rk_stage(self.h, _ptr(Uin), _ptr(U0), _ptr(Uout), int(stage), _ptr(sums),
+                                         _stream()))
+
+    def pack_halo(self, U, idx, buf):
+        """hb_pack_halo: buf[e] = U[idx[e]] (idx: int64 device tensor)."""
+        self._check(self.lib.hb_pack_halo(self.h, _ptr(U), _ptr(idx), int(idx.numel()), _ptr(buf), _stream()))
+        return buf
+
+    def unpack_halo(self, U, idx, buf):
+        """hb_unpack_halo: U[idx[e]] = buf[e]."""
+        self._check(self.lib.hb_unpack_halo(self.h, _ptr(U), _ptr(idx), int(idx.numel()), _ptr(buf), _stream()))
+        return U
 
     def graph_info(self):
         """hb_graph_info: (persist_captured, graph replays, persistent replays,
