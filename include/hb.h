@@ -261,7 +261,9 @@ hb_status hb_adjoint_residual(hb_ctx* ctx, const void* U, const void* psi, doubl
  * driver (one launch per phase, or persistent) and tile shape (32x8, 32x4,
  * 16x8 cells) on a scratch copy of U, keep the fastest, and record it in the
  * cache file ($HB_TUNE_CACHE, default ~/.cache/hbgpu_autotune.txt) keyed by
- * the case signature; hb_create reads that cache.  U is not modified.
+ * the case signature, the device's SM count and the library build (a choice
+ * timed with another build is not reused); hb_create reads that cache.  U is
+ * not modified.
  * Synchronises `stream`.  hb_set_tuning forces a choice (mode 0: per-phase
  * launches, 1: persistent; + 2: separate halo passes before every stage
  * instead of the fused ghost fill, in which each 2D tile writes the ghost

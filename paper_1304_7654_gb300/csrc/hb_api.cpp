@@ -1083,6 +1083,10 @@ hb_status create_impl(const hb_case_desc* descs, int n, hb_ctx** out) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     key += "_sm" + std::to_string(sms);
+    // a choice timed with another build of the kernels is not reused
+    key += std::string("_built ") + __DATE__ + " " + __TIME__;
+    for (char& ch : key)
+      if (ch == ' ') ch = '_';
     ctx->tune_key = key.substr(0, 500);
     int m = (ctx->cases.size() > 1 && ctx->prec == HB_FP32 && ctx->dim == 2 && !ctx->large_ns()) ? 1 : 0;
     int a = 32, b = 8;

@@ -901,6 +901,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   }
 
   // ---- epilogue: HB source and residual or RK update (compile-time N_s)
+  double nacc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if constexpr (!DYN) {
     if (own) {
       own_static();
@@ -925,30 +926,14 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
       }
     }
   }
-  if (MODE == 1 && P.partials) {
-    // FP64 sum of the threads' partials in a fixed order, with few FP64
-    // operations (the FP64 pipe is narrow): the values through shared
-    // memory, 8 lanes per variable each sum a contiguous group, one lane
-    // adds the groups
-    __syncthreads();
-    T* pf = sm;                                                   // primitives are dead here
-    double* pd = reinterpret_cast<double*>(sm + 4 * MAXNT);
 #pragma unroll
-    for (int q = 0; q < NV; ++q) pf[q * nt + tid] = tacc[q];
+  for (int q = 0; q < NV; ++q) nacc[q] = (double)tacc[q];
+  if (MODE == 1 && P.partials) {
     __syncthreads();
-    if (tid < NV * 8) {
-      const int q = tid >> 3, k = tid & 7;
-      const int per = (nt + 7) >> 3;
-      double s = 0.0;
-      for (int e = k * per; e < (k + 1) * per && e < nt; ++e) s += (double)pf[q * nt + e];
-      pd[tid] = s;
-    }
-    __syncthreads();
-    if (tid < NV) {
-      double s = 0.0;
-      for (int k = 0; k < 8; ++k) s += pd[tid * 8 + k];
-      P.partials[(int64_t)t * 8 + tid] = s;
-    }
+    double* scratch = reinterpret_cast<double*>(sm);   // primitives are dead here
+    block_sum8(nacc, NV, scratch);
+    if (threadIdx.x == 0)
+      for (int q = 0; q < NV; ++q) P.partials[(int64_t)t * 8 + q] = nacc[q];
   }
   if (MODE == 1 && P.job_range) fill_tile_ghosts<T, NS>(P, t, B, C);
 }

@@ -36,3 +36,15 @@ def test_oracle_reproduces_its_golden_values(name):
         a, b = np.asarray(got[key], dtype=float), np.asarray(ref[key], dtype=float)
         scale = np.abs(b).max()
         np.testing.assert_allclose(a, b, rtol=1e-11, atol=1e-13 * scale, err_msg=key)
+
+
+def test_oracle_reproduces_its_converged_forces():
+    """The converged-forces fixture (24,000 RK iterations of a small laminar
+    O-grid; the OpenMP build of the oracle, bit for bit the plain one): the
+    run reproduces it, and it is converged (last residual norms below 1e-12)."""
+    with open(os.path.join(GOLDEN, MAKER.CONVERGED_NAME + ".json")) as f:
+        ref = json.load(f)
+    assert max(ref["last_norms"]) < 1e-12
+    got = MAKER.converged_forces()
+    np.testing.assert_allclose(np.asarray(got["forces"]), np.asarray(ref["forces"]), rtol=1e-11, atol=1e-15)
+    assert abs(got["J"] - ref["J"]) <= 1e-13 * max(1.0, abs(ref["J"]))
