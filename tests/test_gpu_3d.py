@@ -117,6 +117,8 @@ def test_full_size_box3d_sampled(prec):
                 got[q, n, v] = R[off + n * st[0] + v * st[1] + (k + 2) * st[2] + (j + 2) * st[3] + (i + 2)]
     err = np.abs(got - Rref) / sc
     q, n, v = np.unravel_index(np.argmax(err), err.shape)
+    print(f"full-size box3d {prec}: max {err.max():.2e}, median {np.median(err):.2e}, "
+          f"per variable {[float(f'{x:.2e}') for x in err.max(axis=(0, 1))]}")
     if prec == "fp64":
         assert err.max() < TOL[prec], (err.max(), tuple(cells[q]), n, v)
         return
