@@ -107,6 +107,8 @@ struct hb_ctx {
   int n_bodies = 0;
   void* d_A = nullptr;          // RK ping-pong and residual scratch
   void* d_B = nullptr;
+  void* d_bal = nullptr;        // 3D: per-snapshot flux balances of an RK stage, [tile][ns][nv][256]
+  size_t bal_bytes = 0;
   double* d_partials = nullptr; // [ntiles][8]
   double* d_face = nullptr;     // [nwall][ns][3]
   double* d_coef = nullptr;     // [ns][nbodies][3]
@@ -611,6 +613,7 @@ void free_ctx(hb_ctx* c) {
   for (int k = 0; k < 4; ++k) cudaFree(c->d_dc[k]);
   cudaFree(c->d_A);
   cudaFree(c->d_B);
+  cudaFree(c->d_bal);
   cudaFree(c->d_partials);
   cudaFree(c->d_face);
   cudaFree(c->d_coef);
@@ -768,6 +771,16 @@ hb_status rebuild_tiles(hb_ctx* c, int TI, int TJ, int mode) {
     HB_CUDA(c, cudaMalloc(&c->d_order, sizeof(int) * std::max(1, n)));
     HB_CUDA(c, cudaMalloc(&c->d_partials, sizeof(double) * 8 * std::max(1, n)));
     c->max_tiles = n;
+  }
+  if (c->dim == 3) {   // balance scratch of the RK stages: every tile's 256 cells x ns x nv
+    const size_t need = (size_t)std::max(1, n) * c->ns_max * c->nv * (8 * 8 * 4) * c->tsize;
+    if (need > c->bal_bytes) {
+      cudaFree(c->d_bal);
+      c->d_bal = nullptr;
+      c->bal_bytes = 0;
+      HB_CUDA(c, cudaMalloc(&c->d_bal, need));
+      c->bal_bytes = need;
+    }
   }
   HB_CUDA(c, cudaMemcpy(c->d_tiles, tiles.data(), sizeof(int4) * n, cudaMemcpyHostToDevice));
   HB_CUDA(c, cudaMemcpy(c->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
@@ -1233,6 +1246,8 @@ hb_status stage_all(hb_ctx* c, hbk::StageParams<T> p, int mode, cudaStream_t s) 
     const T* H = p.H;
     if (p.lam_v == T(0) && ch.ns <= 2 * HB_MAX_STATIC_HARMONICS + 1) p.H = nullptr;
     TimedScope ts(c, 0, s);
+    // the 3D tile parks each snapshot's flux balance in R until its epilogue
+    if (c->dim == 3 && mode == 1) p.R = (T*)c->d_bal + (size_t)ch.tile0 * c->ns_max * c->nv * (8 * 8 * 4);
     if (c->dim == 3) HB_CUDA(c, hbk::launch_stage3d<T>(p, ch.ns, c->viscous, mode, s));
     else HB_CUDA(c, hbk::launch_stage<T>(p, ch.ns, c->viscous, mode, s));
     p.partials = part;

@@ -2,13 +2,16 @@
 // 2D kernel (hb_kernels.cuh) with five conservative variables, three face
 // directions and the full 3x3 Stokes stress.
 //
-// One CTA owns an 8 x 8 x 4 tile of one block and loops over all snapshots;
-// per snapshot it stages primitives (rho, u, v, w, p) and T of the tile plus a
-// 2-cell halo in shared memory, computes Green-Gauss gradients of (u, v, w, T)
-// on the 1-cell ring, then every face of the tile once (MUSCL + van Albada,
-// Roe, viscous), and keeps the flux balance of each own cell in shared
-// memory; the HB source and the RK update run in the epilogue.  Face vectors
-// and centre differences come through the read-only data cache.
+// One CTA owns an 8 x 8 x 4 tile of one block and loops over all snapshots.
+// Once per stage it stages the static geometry in shared memory: 1/V of the
+// region, the low-face vectors of every face the gradient ring and the tile
+// close over, and the centre differences of the tile's faces.  Per snapshot
+// it stages primitives (rho, u, v, w, p) and T of the tile plus a 2-cell halo,
+// computes Green-Gauss gradients of (u, v, w, T) on the 1-cell ring, then
+// every face of the tile once (MUSCL + van Albada, Roe, viscous), and parks
+// the flux balance of each own cell in global memory (the residual output, or
+// a balance scratch in an RK stage); the HB source and the RK update run in
+// the epilogue.
 #pragma once
 
 #include "hb_kernels.cuh"
@@ -115,20 +118,30 @@ __device__ __forceinline__ void visc3d(const T* gL, const T* gR, const T* pL, co
           kap * (g[9] * Sx + g[10] * Sy + g[11] * Sz);
 }
 
+// region (tile + 2-cell halo), gradient ring (tile + 1 cell), faces of the tile
+constexpr int R3I = T3I + 4, R3J = T3J + 4, R3K = T3K + 4, NR3 = R3I * R3J * R3K;
+constexpr int G3I = T3I + 2, G3J = T3J + 2, G3K = T3K + 2, NG3 = G3I * G3J * G3K;
+constexpr int NF3I = (T3I + 1) * T3J * T3K, NF3J = T3I * (T3J + 1) * T3K, NF3K = T3I * T3J * (T3K + 1);
+constexpr int NF3 = NF3I + NF3J + NF3K;
+// low-face vectors along d of the ring box extended by one cell on the high
+// side along d: every face a ring cell closes over, and every face of the tile
+__host__ __device__ constexpr int sbox3_i(int d) { return G3I + (d == 0); }
+__host__ __device__ constexpr int sbox3_j(int d) { return G3J + (d == 1); }
+__host__ __device__ constexpr int sbox3_n(int d) { return sbox3_i(d) * sbox3_j(d) * (G3K + (d == 2)); }
+__host__ __device__ constexpr int sbox3_off(int d) { return d == 0 ? 0 : (d == 1 ? 3 * sbox3_n(0) : 3 * (sbox3_n(0) + sbox3_n(1))); }
+constexpr int NSB3 = 3 * (sbox3_n(0) + sbox3_n(1) + sbox3_n(2));
+
 __host__ __device__ constexpr size_t tile3d_smem_elems(int NS) {
-  return (size_t)7 * (T3I + 4) * (T3J + 4) * (T3K + 4) + (size_t)12 * (T3I + 2) * (T3J + 2) * (T3K + 2) +
-         (size_t)5 * ((T3I + 1) * T3J * T3K + T3I * (T3J + 1) * T3K + T3I * T3J * (T3K + 1)) +
-         (size_t)NS * 5 * T3I * T3J * T3K + (size_t)NS * NS;
+  return (size_t)7 * NR3 + (size_t)12 * NG3 + (size_t)5 * NF3 + (size_t)NSB3 + (size_t)3 * NF3 + (size_t)NS * NS;
 }
 
 template <typename T, int NS, bool VISC, int MODE>
 __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
   constexpr int NV = 5;
   constexpr int TI = T3I, TJ = T3J, TK = T3K, NT = TI * TJ * TK;
-  constexpr int RI = TI + 4, RJ = TJ + 4, RK = TK + 4, NR = RI * RJ * RK;
-  constexpr int GI = TI + 2, GJ = TJ + 2, GK = TK + 2, NG = GI * GJ * GK;
-  constexpr int NFI = (TI + 1) * TJ * TK, NFJ = TI * (TJ + 1) * TK, NFK = TI * TJ * (TK + 1);
-  constexpr int NF = NFI + NFJ + NFK;
+  constexpr int RI = R3I, RJ = R3J, NR = NR3;
+  constexpr int GI = G3I, GJ = G3J, NG = NG3;
+  constexpr int NFI = NF3I, NFJ = NF3J, NF = NF3;
   const int4 tl = P.tiles[t];
   const BlockDev B = P.blocks[tl.x];
   const CaseDev<T>* C = P.cases + B.cs;
@@ -143,29 +156,60 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
   T* sIV = sRT + 2 * NR;   // [NR]
   T* sG = sIV + NR;        // [12][NG]
   T* sF = sG + 12 * NG;    // [NV][NF]
-  T* sAcc = sF + NV * NF;  // [NS][NV][NT]
-  T* sD = sAcc + NS * NV * NT;
+  T* sSb = sF + NV * NF;   // [d][3][box of d] static low-face vectors
+  T* sDC = sSb + NSB3;     // [3][NF] static centre differences of the tile's faces
+  T* sD = sDC + 3 * NF;    // [NS][NS]
 
   const T gam = C->gamma, gm1 = C->gamma - T(1), eps = C->eps, efrac = C->ent_frac;
   const T gg1 = gam / gm1, hef = T(0.5) / efrac;
   const T mu = C->mu, kap = C->kappa, omega = C->omega;
   const int efix = C->entropy_fix;
   const bool moving = C->motion != 0;
-  const T* gS[3][3];
-  const T* gDc[3][3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) { gS[d][a] = P.g.q[G_S + 3 * d + a] + B.goff; gDc[d][a] = P.g.q[G_DC + 3 * d + a] + B.goff; }
 
   auto rcell = [&](int ri, int rj, int rk) { return (rk * RJ + rj) * RI + ri; };
   auto pcell = [&](int i, int j, int k) -> int64_t { return (int64_t)(k + 2) * sK + (int64_t)(j + 2) * sJ + (i + 2); };
   auto inpad = [&](int i, int j, int k) { return i <= n0 + 1 && j <= n1 + 1 && k <= n2 + 1; };
+  // storage index of ring-box position (gi, gj, gk) (cell i0-1+gi, ...) in the face-vector box of d
+  auto sbidx = [&](int d, int gi, int gj, int gk) { return (gk * sbox3_j(d) + gj) * sbox3_i(d) + gi; };
+  // face work item fq -> direction and the tile position of the cell whose low face it is
+  auto face_of = [&](int fq, int& d, int& fi, int& fj, int& fk) {
+    if (fq < NFI) { d = 0; fi = fq % (TI + 1); fj = (fq / (TI + 1)) % TJ; fk = fq / ((TI + 1) * TJ); }
+    else if (fq < NFI + NFJ) { const int q2 = fq - NFI; d = 1; fi = q2 % TI; fj = (q2 / TI) % (TJ + 1); fk = q2 / (TI * (TJ + 1)); }
+    else { const int q3 = fq - NFI - NFJ; d = 2; fi = q3 % TI; fj = (q3 / TI) % TJ; fk = q3 / (TI * TJ); }
+  };
+  auto face_used = [&](int d, int Ri, int Rj, int Rk) {
+    return !(Ri > n0 - (d != 0) || Rj > n1 - (d != 1) || Rk > n2 - (d != 2));
+  };
 
+  // ---- static geometry, once per stage: 1/V of the region, the low-face
+  // vectors of the ring boxes and the centre differences of the tile's faces
   for (int r = tid; r < NR; r += nt) {
     const int ri = r % RI, rj = (r / RI) % RJ, rk = r / (RI * RJ);
     const int i = i0 - 2 + ri, j = j0 - 2 + rj, k = k0 - 2 + rk;
     sIV[r] = inpad(i, j, k) ? Ar<T>::rcp(P.g.q[G_VOL][B.goff + pcell(i, j, k)]) : T(1);
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int EI = sbox3_i(d), EJ = sbox3_j(d), NB = sbox3_n(d);
+    T* Sd = sSb + sbox3_off(d);
+    for (int e = tid; e < NB; e += nt) {
+      const int gi = e % EI, gj = (e / EI) % EJ, gk = e / (EI * EJ);
+      const int i = i0 - 1 + gi, j = j0 - 1 + gj, k = k0 - 1 + gk;
+      const bool in = inpad(i, j, k);
+      const int64_t c = B.goff + pcell(i, j, k);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Sd[a * NB + e] = in ? P.g.q[G_S + 3 * d + a][c] : T(0);
+    }
+  }
+  if (VISC) {
+    for (int fq = tid; fq < NF; fq += nt) {
+      int d, fi, fj, fk;
+      face_of(fq, d, fi, fj, fk);
+      const bool use = face_used(d, i0 + fi, j0 + fj, k0 + fk);
+      const int64_t c = B.goff + pcell(i0 + fi, j0 + fj, k0 + fk);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) sDC[a * NF + fq] = use ? P.g.q[G_DC + 3 * d + a][c] : T(1);
+    }
   }
   for (int e = tid; e < NS * NS; e += nt) sD[e] = C->D[e];
 
@@ -174,36 +218,60 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
   const bool own = (tid < NT) && ci < n0 && cj < n1 && ck < n2;
   const int rown = rcell(ti + 2, tj + 2, tk + 2);
   const int64_t cown = pcell(ci, cj, ck);
+  // where the flux balance of the own cell at snapshot n waits for the
+  // epilogue: in the residual output itself, or (RK stage) in this tile's
+  // slice of the balance scratch, [n][q][thread], whose 128-byte lines belong
+  // to one warp each and are discarded from L2 once read back
+  T* const bal = (MODE == 1) ? P.R + (int64_t)t * NS * NV * NT : P.R;
+  auto bal_at = [&](int n, int q) -> T& {
+    if constexpr (MODE == 1) return bal[(n * NV + q) * NT + tid];
+    else return P.R[B.off + ((int64_t)n * NV + q) * B.plane + cown];
+  };
 
   for (int n = 0; n < NS; ++n) {
     const Fr<T> f = frame_at(C, n);
     __syncthreads();
-    for (int r = tid; r < NR; r += nt) {
-      const int ri = r % RI, rj = (r / RI) % RJ, rk = r / (RI * RJ);
-      const int i = i0 - 2 + ri, j = j0 - 2 + rj, k = k0 - 2 + rk;
-      T w[5] = {T(1), T(0), T(0), T(0), T(1)}, tt = gam;
-      if (inpad(i, j, k)) {
-        const T* u = P.Uprev + B.off + (int64_t)n * NV * B.plane + pcell(i, j, k);
-        const T rho = u[0], ir = Ar<T>::rcp(rho);
-        w[0] = rho;
-        w[1] = u[B.plane] * ir;
-        w[2] = u[2 * B.plane] * ir;
-        w[3] = u[3 * B.plane] * ir;
-        w[4] = gm1 * (u[4 * B.plane] - T(0.5) * rho * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]));
-        tt = gam * w[4] * ir;
+    // the region at snapshot n: every load of a thread's cells issued before
+    // the first is used (one L2 latency per snapshot instead of one per cell)
+    {
+      constexpr int NRT = (NR + NT - 1) / NT;   // cells per thread (blockDim.x = NT)
+      T uq[NRT][5];
+#pragma unroll
+      for (int it = 0; it < NRT; ++it) {
+        const int r = tid + it * NT;
+        const int ri = r % RI, rj = (r / RI) % RJ, rk = r / (RI * RJ);
+        const int i = i0 - 2 + ri, j = j0 - 2 + rj, k = k0 - 2 + rk;
+        if (r < NR && inpad(i, j, k)) {
+          const T* u = P.Uprev + B.off + (int64_t)n * NV * B.plane + pcell(i, j, k);
+#pragma unroll
+          for (int q = 0; q < 5; ++q) uq[it][q] = u[q * B.plane];
+        } else {   // outside the padded block: a benign state, never used by own cells
+          uq[it][0] = T(1);
+          uq[it][1] = uq[it][2] = uq[it][3] = T(0);
+          uq[it][4] = T(1) / gm1;
+        }
       }
-      sts4(sW + 4 * r, w[1], w[2], w[3], w[4]);
-      sts2(sRT + 2 * r, w[0], tt);
+#pragma unroll
+      for (int it = 0; it < NRT; ++it) {
+        const int r = tid + it * NT;
+        if (r < NR) {
+          const T rho = uq[it][0], ir = Ar<T>::rcp(rho);
+          const T u = uq[it][1] * ir, v = uq[it][2] * ir, w = uq[it][3] * ir;
+          const T p = gm1 * (uq[it][4] - T(0.5) * rho * (u * u + v * v + w * w));
+          sts4(sW + 4 * r, u, v, w, p);
+          sts2(sRT + 2 * r, rho, gam * p * ir);
+        }
+      }
     }
     __syncthreads();
     if (VISC) {
+      // Green-Gauss gradients of (u, v, w, T) on the ring, as the closed-cell
+      // sum of (phi_nb - phi_c)/2 S with the static face vectors, rotated once
+      // per quantity into the frame of snapshot n (the sum is linear in S)
       for (int gq = tid; gq < NG; gq += nt) {
         const int gi = gq % GI, gj = (gq / GI) % GJ, gk = gq / (GI * GJ);
         const int r = rcell(gi + 1, gj + 1, gk + 1);
         const int i = i0 - 1 + gi, j = j0 - 1 + gj, k = k0 - 1 + gk;
-        T g[12];
-#pragma unroll
-        for (int q = 0; q < 12; ++q) g[q] = T(0);
         // ring cells beyond index n are never L or R of a computed face; their
         // high faces would lie outside the padded block
         if (i > n0 || j > n1 || k > n2) {
@@ -211,45 +279,51 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
           for (int q = 0; q < 12; ++q) sG[q * NG + gq] = T(0);
           continue;
         }
+        T g[12];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) g[q] = T(0);
         T pc[4], pdum;
         lds4(sW + 4 * r, pc[0], pc[1], pc[2], pdum);
         pc[3] = sRT[2 * r + 1];
         const int rs[3] = {1, RI, RI * RJ};
-        const int64_t cs[3] = {1, sJ, sK};
-        const int64_t c = pcell(i, j, k);
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
+        for (int d = 0; d < 3; ++d) {
+          const T* Sd = sSb + sbox3_off(d);
+          const int NB = sbox3_n(d);
+          const int lo = sbidx(d, gi, gj, gk);
+          const int hi = lo + (d == 0 ? 1 : (d == 1 ? sbox3_i(1) : sbox3_i(2) * sbox3_j(2)));
 #pragma unroll
           for (int side = 0; side < 2; ++side) {
             const int o = side ? r + rs[d] : r - rs[d];
-            const int64_t fc = side ? c + cs[d] : c;      // owner of the face
-            const T s0 = __ldg(gS[d][0] + fc), s1 = __ldg(gS[d][1] + fc), s2 = __ldg(gS[d][2] + fc);
-            T sx, sy;
-            rotv(f, s0, s1, sx, sy);
-            const T sg = side ? T(0.5) : T(-0.5);
-            const T sv[3] = {sg * sx, sg * sy, sg * s2};
+            const int e = side ? hi : lo;
+            const T sv[3] = {Sd[e], Sd[NB + e], Sd[2 * NB + e]};
             T po[4];
             lds4(sW + 4 * o, po[0], po[1], po[2], po[3]);
             const T dphi[4] = {po[0] - pc[0], po[1] - pc[1], po[2] - pc[2], sRT[2 * o + 1] - pc[3]};
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
-              for (int a = 0; a < 3; ++a) g[3 * q + a] += dphi[q] * sv[a];
+              for (int a = 0; a < 3; ++a) g[3 * q + a] = side ? g[3 * q + a] + dphi[q] * sv[a] : g[3 * q + a] - dphi[q] * sv[a];
           }
-        const T iv = sIV[r];
+        }
+        const T hiv = T(0.5) * sIV[r];
 #pragma unroll
-        for (int q = 0; q < 12; ++q) sG[q * NG + gq] = g[q] * iv;
+        for (int q = 0; q < 4; ++q) {
+          T gx = g[3 * q], gy = g[3 * q + 1];
+          if (moving) rotv(f, g[3 * q], g[3 * q + 1], gx, gy);
+          sG[(3 * q) * NG + gq] = gx * hiv;
+          sG[(3 * q + 1) * NG + gq] = gy * hiv;
+          sG[(3 * q + 2) * NG + gq] = g[3 * q + 2] * hiv;
+        }
       }
       __syncthreads();
     }
     for (int fq = tid; fq < NF; fq += nt) {
       int d, fi, fj, fk;
-      if (fq < NFI) { d = 0; fi = fq % (TI + 1); fj = (fq / (TI + 1)) % TJ; fk = fq / ((TI + 1) * TJ); }
-      else if (fq < NFI + NFJ) { const int q2 = fq - NFI; d = 1; fi = q2 % TI; fj = (q2 / TI) % (TJ + 1); fk = q2 / (TI * (TJ + 1)); }
-      else { const int q3 = fq - NFI - NFJ; d = 2; fi = q3 % TI; fj = (q3 / TI) % TJ; fk = q3 / (TI * TJ); }
+      face_of(fq, d, fi, fj, fk);
       // the face is the low face of cell R = (i0+fi, j0+fj, k0+fk) along d
       const int Ri = i0 + fi, Rj = j0 + fj, Rk = k0 + fk;
-      if (Ri > n0 - (d != 0) || Rj > n1 - (d != 1) || Rk > n2 - (d != 2)) continue;
+      if (!face_used(d, Ri, Rj, Rk)) continue;
       const int st = (d == 0) ? 1 : (d == 1 ? RI : RI * RJ);
       const int rR = rcell(fi + 2, fj + 2, fk + 2);
       const int rL = rR - st;
@@ -272,12 +346,16 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
         rhoR = c - T(0.5) * van_albada_w(d1, d2, w1, va_weight(d2, eps));
       }
       const T WL[5] = {rhoL, uvL.x, uvL.y, wpL.x, wpL.y}, WR[5] = {rhoR, uvR.x, uvR.y, wpR.x, wpR.y};
-      const int64_t gR = pcell(Ri, Rj, Rk);
+      const T* Sd = sSb + sbox3_off(d);
+      const int NB = (d == 0) ? sbox3_n(0) : (d == 1 ? sbox3_n(1) : sbox3_n(2));
+      const int eR = (d == 0) ? sbidx(0, fi + 1, fj + 1, fk + 1)
+                              : (d == 1 ? sbidx(1, fi + 1, fj + 1, fk + 1) : sbidx(2, fi + 1, fj + 1, fk + 1));
       T sx, sy;
-      rotv(f, __ldg(gS[d][0] + gR), __ldg(gS[d][1] + gR), sx, sy);
-      const T sz = __ldg(gS[d][2] + gR);
+      rotv(f, Sd[eR], Sd[NB + eR], sx, sy);
+      const T sz = Sd[2 * NB + eR];
       T vgn = T(0);
       if (moving) {
+        const int64_t gR = pcell(Ri, Rj, Rk);
         T xf, yf;
         rotp(f, __ldg(P.g.q[G_XF + 3 * d] + B.goff + gR), __ldg(P.g.q[G_XF + 3 * d + 1] + B.goff + gR), xf, yf);
         const T vgx = -f.thd * (yf - f.py), vgy = f.thd * (xf - f.px);
@@ -294,8 +372,8 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
 #pragma unroll
         for (int q = 0; q < 12; ++q) { gl[q] = sG[q * NG + gLi]; gr[q] = sG[q * NG + gRi]; }
         T tx, ty;
-        rotv(f, __ldg(gDc[d][0] + gR), __ldg(gDc[d][1] + gR), tx, ty);
-        const T tz = __ldg(gDc[d][2] + gR);
+        rotv(f, sDC[fq], sDC[NF + fq], tx, ty);
+        const T tz = sDC[2 * NF + fq];
         const T pL[4] = {uvb.x, uvb.y, wpb.x, sRT[2 * rL + 1]};
         const T pR[4] = {uvc.x, uvc.y, wpc.x, sRT[2 * rR + 1]};
         T Fv[5];
@@ -307,15 +385,17 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
       for (int q = 0; q < 5; ++q) sF[q * NF + fq] = F[q];
     }
     __syncthreads();
+    // flux balance of the own cell at snapshot n, parked in global memory
+    // until the epilogue adds the HB source (the shared memory goes to the
+    // static face geometry)
     if (own) {
       const int fi0 = (tk * TJ + tj) * (TI + 1) + ti;
       const int fj0 = NFI + (tk * (TJ + 1) + tj) * TI + ti;
       const int fk0 = NFI + NFJ + (tk * TJ + tj) * TI + ti;
 #pragma unroll
       for (int q = 0; q < NV; ++q)
-        sAcc[(n * NV + q) * NT + tid] = (sF[q * NF + fi0 + 1] - sF[q * NF + fi0]) +
-                                        (sF[q * NF + fj0 + TI] - sF[q * NF + fj0]) +
-                                        (sF[q * NF + fk0 + TI * TJ] - sF[q * NF + fk0]);
+        bal_at(n, q) = (sF[q * NF + fi0 + 1] - sF[q * NF + fi0]) + (sF[q * NF + fj0 + TI] - sF[q * NF + fj0]) +
+                       (sF[q * NF + fk0 + TI * TJ] - sF[q * NF + fk0]);
     }
   }
 
@@ -333,24 +413,27 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
 #pragma unroll
       for (int q = 0; q < NV; ++q) uu[m][q] = P.Uprev[B.off + ((int64_t)m * NV + q) * B.plane + cown];
     T Sb[3][3], m2[3], mg[3];
-    const int64_t cs[3] = {1, sJ, sK};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
+      const T* Sd = sSb + sbox3_off(d);
+      const int NB = sbox3_n(d);
+      const int lo = sbidx(d, ti + 1, tj + 1, tk + 1);
+      const int hi = lo + (d == 0 ? 1 : (d == 1 ? sbox3_i(1) : sbox3_i(2) * sbox3_j(2)));
 #pragma unroll
-      for (int a = 0; a < 3; ++a) Sb[d][a] = T(0.5) * (__ldg(gS[d][a] + cown) + __ldg(gS[d][a] + cown + cs[d]));
+      for (int a = 0; a < 3; ++a) Sb[d][a] = T(0.5) * (Sd[a * NB + lo] + Sd[a * NB + hi]);
       m2[d] = Sb[d][0] * Sb[d][0] + Sb[d][1] * Sb[d][1] + Sb[d][2] * Sb[d][2];
       mg[d] = m2[d] * Ar<T>::rsq(m2[d]);
     }
     for (int n = 0; n < NS; ++n) {
+      const int64_t base = B.off + (int64_t)n * NV * B.plane + cown;
       T Rn[NV];
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
         T h = T(0);
 #pragma unroll
         for (int m = 0; m < NS; ++m) h += sD[n * NS + m] * uu[m][q];
-        Rn[q] = sAcc[(n * NV + q) * NT + tid] + vw * h;
+        Rn[q] = bal_at(n, q) + vw * h;
       }
-      const int64_t base = B.off + (int64_t)n * NV * B.plane + cown;
       if (MODE == 0) {
 #pragma unroll
         for (int q = 0; q < NV; ++q) P.R[base + q * B.plane] = Rn[q];
@@ -394,6 +477,17 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
           }
         }
       }
+    }
+  }
+  if constexpr (MODE == 1) {
+    // the parked balances are dead: drop their L2 lines unwritten (every lane
+    // of the warp has read its values before the barrier)
+    __syncwarp();
+    constexpr int LPP = (32 * (int)sizeof(T)) / 128;   // 128-byte lines per warp and (n, q)
+    const int lane = tid & 31;
+    for (int e = lane; e < NS * NV * LPP; e += 32) {
+      const T* line = bal + (e / LPP) * NT + (tid & ~31) + (e % LPP) * (128 / (int)sizeof(T));
+      asm volatile("discard.global.L2 [%0], 128;" ::"l"(line) : "memory");
     }
   }
 #pragma unroll
