@@ -615,22 +615,42 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   // primitives of region cell r at snapshot n into buffer b (the limiter
   // acts on the Cartesian velocity components of the inertial frame, so the
   // velocity is staged in that frame and the metrics are rotated instead)
-  auto stage_cell = [&](int r, int n, int b) {
+  struct Q4 { T x, y, z, w; };   // conservative variables of one cell
+  auto load_cell = [&](int r, int n) -> Q4 {
     const int ri = r % RI, rj = r / RI;
     const int i = i0 - 2 + ri, j = j0 - 2 + rj;
-    T w0 = T(1), w1 = T(0), w2 = T(0), w3 = T(1), tt = gam;
-    if (i <= n0 + 1 && j <= n1 + 1) {
+    Q4 q;
+    if (r < NRt && i <= n0 + 1 && j <= n1 + 1) {
       const T* u = P.Uprev + B.off + (int64_t)n * NV * B.plane + (int64_t)(j + 2) * P0 + (i + 2);
-      const T rho = u[0], mx = u[B.plane], my = u[2 * B.plane], E = u[3 * B.plane];
-      const T ir = Ar<T>::rcp(rho);
-      w0 = rho;
-      w1 = mx * ir;
-      w2 = my * ir;
-      w3 = gm1 * (E - T(0.5) * rho * (w1 * w1 + w2 * w2));
-      tt = gam * w3 * ir;
+      q.x = u[0];
+      q.y = u[B.plane];
+      q.z = u[2 * B.plane];
+      q.w = u[3 * B.plane];
+    } else {   // outside the padded block: a benign state, never used by own cells
+      q.x = T(1);
+      q.y = q.z = T(0);
+      q.w = T(1) / gm1;
     }
-    sts4(sW + (b * NR + r) * 4, w1, w2, w0, w3);
-    sT[b * NR + r] = tt;
+    return q;
+  };
+  auto store_cell = [&](int r, int b, Q4 q) {
+    const T rho = q.x;
+    const T ir = Ar<T>::rcp(rho);
+    const T w1 = q.y * ir, w2 = q.z * ir;
+    const T w3 = gm1 * (q.w - T(0.5) * rho * (w1 * w1 + w2 * w2));
+    sts4(sW + (b * NR + r) * 4, w1, w2, rho, w3);
+    sT[b * NR + r] = gam * w3 * ir;
+  };
+  // region cells r0, r0 + nt, ... (< NRt) at snapshot n into buffer b: every
+  // load of the thread issued before the first is used
+  constexpr int NSTG = (NR + NT - 1) / NT;
+  auto stage_cells = [&](int r0, int n, int b) {
+    Q4 q[NSTG];
+#pragma unroll
+    for (int it = 0; it < NSTG; ++it) q[it] = load_cell(r0 + it * nt, n);
+#pragma unroll
+    for (int it = 0; it < NSTG; ++it)
+      if (r0 + it * nt < NRt) store_cell(r0 + it * nt, b, q[it]);
   };
 
   // Green-Gauss gradients of (u, v, T) at ring cell gq from buffer b, written
@@ -857,7 +877,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
     // prologue: snapshot 0 staged (and its gradients); then per snapshot two
     // phases: (A) faces of n + staging of n+1, (B) balance of n + gradients
     // of n+1
-    for (int r = tid; r < NRt; r += nt) stage_cell(r, 0, 0);
+    stage_cells(tid, 0, 0);
     __syncthreads();
     if (VISC) {
       const Fr<T> f0 = frame_at(C, 0);
@@ -872,8 +892,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
       // fewer takes a region cell first
       int w = tid;
       for (; w < NF; w += nt) face(w, f, b);
-      if (next)
-        for (w -= NF; w < NRt; w += nt) stage_cell(w, n + 1, b ^ 1);
+      if (next) stage_cells(w - NF, n + 1, b ^ 1);
       __syncthreads();
       accumulate(n);
       if (VISC && next) {
@@ -887,7 +906,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
     // needs no barrier after the balance of n (which reads only the fluxes)
     for (int n = 0; n < ns; ++n) {
       const Fr<T> f = frame_at(C, n);
-      for (int r = tid; r < NRt; r += nt) stage_cell(r, n, 0);
+      stage_cells(tid, n, 0);
       __syncthreads();
       if (VISC) {
         for (int gq = tid; gq < NGt; gq += nt) grad_cell(gq, f, 0);

@@ -154,7 +154,7 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
   T* sW = sm;              // [NR][4] (u, v, w, p) of each cell
   T* sRT = sW + 4 * NR;    // [NR][2] (rho, T = gamma p / rho)
   T* sIV = sRT + 2 * NR;   // [NR]
-  T* sG = sIV + NR;        // [12][NG]
+  T* sG = sIV + NR;        // [NG][12] gradients of (u, v, w, T), (x, y, z) each
   T* sF = sG + 12 * NG;    // [NV][NF]
   T* sSb = sF + NV * NF;   // [d][3][box of d] static low-face vectors
   T* sDC = sSb + NSB3;     // [3][NF] static centre differences of the tile's faces
@@ -183,33 +183,62 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
 
   // ---- static geometry, once per stage: 1/V of the region, the low-face
   // vectors of the ring boxes and the centre differences of the tile's faces
-  for (int r = tid; r < NR; r += nt) {
-    const int ri = r % RI, rj = (r / RI) % RJ, rk = r / (RI * RJ);
-    const int i = i0 - 2 + ri, j = j0 - 2 + rj, k = k0 - 2 + rk;
-    sIV[r] = inpad(i, j, k) ? Ar<T>::rcp(P.g.q[G_VOL][B.goff + pcell(i, j, k)]) : T(1);
-  }
+  // (every load of a thread issued before the first is used; blockDim.x = NT)
+  {
+    constexpr int ITR = (NR + NT - 1) / NT;
+    constexpr int ITS = (sbox3_n(2) + NT - 1) / NT;   // the largest of the three boxes
+    T vq[ITR], sq[3][ITS][3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int EI = sbox3_i(d), EJ = sbox3_j(d), NB = sbox3_n(d);
-    T* Sd = sSb + sbox3_off(d);
-    for (int e = tid; e < NB; e += nt) {
-      const int gi = e % EI, gj = (e / EI) % EJ, gk = e / (EI * EJ);
-      const int i = i0 - 1 + gi, j = j0 - 1 + gj, k = k0 - 1 + gk;
-      const bool in = inpad(i, j, k);
-      const int64_t c = B.goff + pcell(i, j, k);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) Sd[a * NB + e] = in ? P.g.q[G_S + 3 * d + a][c] : T(0);
+    for (int it = 0; it < ITR; ++it) {
+      const int r = tid + it * NT;
+      const int ri = r % RI, rj = (r / RI) % RJ, rk = r / (RI * RJ);
+      const int i = i0 - 2 + ri, j = j0 - 2 + rj, k = k0 - 2 + rk;
+      vq[it] = (r < NR && inpad(i, j, k)) ? P.g.q[G_VOL][B.goff + pcell(i, j, k)] : T(1);
     }
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int it = 0; it < ITS; ++it) {
+        const int e = tid + it * NT;
+        const int EI = sbox3_i(d), EJ = sbox3_j(d);
+        const int gi = e % EI, gj = (e / EI) % EJ, gk = e / (EI * EJ);
+        const int i = i0 - 1 + gi, j = j0 - 1 + gj, k = k0 - 1 + gk;
+        const bool in = e < sbox3_n(d) && inpad(i, j, k);
+        const int64_t c = B.goff + pcell(i, j, k);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sq[d][it][a] = in ? P.g.q[G_S + 3 * d + a][c] : T(0);
+      }
+#pragma unroll
+    for (int it = 0; it < ITR; ++it)
+      if (tid + it * NT < NR) sIV[tid + it * NT] = Ar<T>::rcp(vq[it]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int it = 0; it < ITS; ++it) {
+        const int e = tid + it * NT;
+        if (e < sbox3_n(d))
+#pragma unroll
+          for (int a = 0; a < 3; ++a) sSb[sbox3_off(d) + a * sbox3_n(d) + e] = sq[d][it][a];
+      }
   }
   if (VISC) {
-    for (int fq = tid; fq < NF; fq += nt) {
+    constexpr int ITF = (NF + NT - 1) / NT;
+    T dq[ITF][3];
+#pragma unroll
+    for (int it = 0; it < ITF; ++it) {
+      const int fq = tid + it * NT;
       int d, fi, fj, fk;
       face_of(fq, d, fi, fj, fk);
-      const bool use = face_used(d, i0 + fi, j0 + fj, k0 + fk);
+      const bool use = fq < NF && face_used(d, i0 + fi, j0 + fj, k0 + fk);
       const int64_t c = B.goff + pcell(i0 + fi, j0 + fj, k0 + fk);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) sDC[a * NF + fq] = use ? P.g.q[G_DC + 3 * d + a][c] : T(1);
+      for (int a = 0; a < 3; ++a) dq[it][a] = use ? P.g.q[G_DC + 3 * d + a][c] : T(1);
     }
+#pragma unroll
+    for (int it = 0; it < ITF; ++it)
+      if (tid + it * NT < NF)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sDC[a * NF + tid + it * NT] = dq[it][a];
   }
   for (int e = tid; e < NS * NS; e += nt) sD[e] = C->D[e];
 
@@ -276,7 +305,7 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
         // high faces would lie outside the padded block
         if (i > n0 || j > n1 || k > n2) {
 #pragma unroll
-          for (int q = 0; q < 12; ++q) sG[q * NG + gq] = T(0);
+          for (int q = 0; q < 3; ++q) sts4(sG + 12 * gq + 4 * q, T(0), T(0), T(0), T(0));
           continue;
         }
         T g[12];
@@ -307,14 +336,17 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
           }
         }
         const T hiv = T(0.5) * sIV[r];
+        T go[12];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           T gx = g[3 * q], gy = g[3 * q + 1];
           if (moving) rotv(f, g[3 * q], g[3 * q + 1], gx, gy);
-          sG[(3 * q) * NG + gq] = gx * hiv;
-          sG[(3 * q + 1) * NG + gq] = gy * hiv;
-          sG[(3 * q + 2) * NG + gq] = g[3 * q + 2] * hiv;
+          go[3 * q] = gx * hiv;
+          go[3 * q + 1] = gy * hiv;
+          go[3 * q + 2] = g[3 * q + 2] * hiv;
         }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) sts4(sG + 12 * gq + 4 * q, go[4 * q], go[4 * q + 1], go[4 * q + 2], go[4 * q + 3]);
       }
       __syncthreads();
     }
@@ -370,7 +402,10 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
         const int gLi = gRi - gs;
         T gl[12], gr[12];
 #pragma unroll
-        for (int q = 0; q < 12; ++q) { gl[q] = sG[q * NG + gLi]; gr[q] = sG[q * NG + gRi]; }
+        for (int q = 0; q < 3; ++q) {
+          lds4(sG + 12 * gLi + 4 * q, gl[4 * q], gl[4 * q + 1], gl[4 * q + 2], gl[4 * q + 3]);
+          lds4(sG + 12 * gRi + 4 * q, gr[4 * q], gr[4 * q + 1], gr[4 * q + 2], gr[4 * q + 3]);
+        }
         T tx, ty;
         rotv(f, sDC[fq], sDC[NF + fq], tx, ty);
         const T tz = sDC[2 * NF + fq];
