@@ -586,22 +586,40 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   const bool moving = C->motion != 0;
 
   // ---- static geometry of the region (tile + 2-cell halo), once per stage
-  for (int r = tid; r < NRt; r += nt) {
-    const int ri = r % RI, rj = r / RI;
-    const int i = i0 - 2 + ri, j = j0 - 2 + rj;
-    if (i <= n0 + 1 && j <= n1 + 1) {
-      const int64_t c = B.goff + (int64_t)(j + 2) * P0 + (i + 2);
-      sIV[r] = Ar<T>::rcp(P.g.q[G_VOL][c]);
-      sS[r] = P.g.q[G_S + 0][c];
-      sS[NR + r] = P.g.q[G_S + 1][c];
-      sS[2 * NR + r] = P.g.q[G_S + 3][c];
-      sS[3 * NR + r] = P.g.q[G_S + 4][c];
-    } else {   // outside the padded block: a benign unit cell, never used by own cells
-      sIV[r] = T(1);
-      sS[r] = T(1);
-      sS[NR + r] = T(0);
-      sS[2 * NR + r] = T(0);
-      sS[3 * NR + r] = T(1);
+  // (every load of a thread issued before the first is used)
+  {
+    constexpr int NGEO = (NR + NT - 1) / NT;
+    T gq[NGEO][5];
+#pragma unroll
+    for (int it = 0; it < NGEO; ++it) {
+      const int r = tid + it * nt;
+      const int ri = r % RI, rj = r / RI;
+      const int i = i0 - 2 + ri, j = j0 - 2 + rj;
+      if (r < NRt && i <= n0 + 1 && j <= n1 + 1) {
+        const int64_t c = B.goff + (int64_t)(j + 2) * P0 + (i + 2);
+        gq[it][0] = P.g.q[G_VOL][c];
+        gq[it][1] = P.g.q[G_S + 0][c];
+        gq[it][2] = P.g.q[G_S + 1][c];
+        gq[it][3] = P.g.q[G_S + 3][c];
+        gq[it][4] = P.g.q[G_S + 4][c];
+      } else {   // outside the padded block: a benign unit cell, never used by own cells
+        gq[it][0] = T(1);
+        gq[it][1] = T(1);
+        gq[it][2] = T(0);
+        gq[it][3] = T(0);
+        gq[it][4] = T(1);
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < NGEO; ++it) {
+      const int r = tid + it * nt;
+      if (r < NRt) {
+        sIV[r] = Ar<T>::rcp(gq[it][0]);
+        sS[r] = gq[it][1];
+        sS[NR + r] = gq[it][2];
+        sS[2 * NR + r] = gq[it][3];
+        sS[3 * NR + r] = gq[it][4];
+      }
     }
   }
   for (int e = tid; e < NS * NS; e += nt) sD[e] = C->D[e];

@@ -140,7 +140,8 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
   constexpr int NV = 5;
   constexpr int TI = T3I, TJ = T3J, TK = T3K, NT = TI * TJ * TK;
   constexpr int RI = R3I, RJ = R3J, NR = NR3;
-  constexpr int GI = G3I, GJ = G3J, NG = NG3;
+  constexpr int GI = G3I, GJ = G3J, GK = G3K, NG = NG3;
+  constexpr int NGU = TI * TJ * TK + 2 * (TJ * TK + TI * TK + TI * TJ);
   constexpr int NFI = NF3I, NFJ = NF3J, NF = NF3;
   const int4 tl = P.tiles[t];
   const BlockDev B = P.blocks[tl.x];
@@ -154,7 +155,7 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
   T* sW = sm;              // [NR][4] (u, v, w, p) of each cell
   T* sRT = sW + 4 * NR;    // [NR][2] (rho, T = gamma p / rho)
   T* sIV = sRT + 2 * NR;   // [NR]
-  T* sG = sIV + NR;        // [NG][12] gradients of (u, v, w, T), (x, y, z) each
+  T* sG = sIV + NR;        // [NG][12] gradients of (u, v, w, T), (x, y, z) each, ring box order
   T* sF = sG + 12 * NG;    // [NV][NF]
   T* sSb = sF + NV * NF;   // [d][3][box of d] static low-face vectors
   T* sDC = sSb + NSB3;     // [3][NF] static centre differences of the tile's faces
@@ -297,8 +298,24 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
       // Green-Gauss gradients of (u, v, w, T) on the ring, as the closed-cell
       // sum of (phi_nb - phi_c)/2 S with the static face vectors, rotated once
       // per quantity into the frame of snapshot n (the sum is linear in S)
-      for (int gq = tid; gq < NG; gq += nt) {
-        const int gi = gq % GI, gj = (gq / GI) % GJ, gk = gq / (GI * GJ);
+      // only the ring cells that are L or R of a tile face: the tile and its
+      // six face-adjacent slabs (the ring's edges and corners are never read),
+      // NGU = 512 work items, two full rounds of the 256 threads
+      for (int w = tid; w < NGU; w += nt) {
+        int gi, gj, gk;
+        if (w < NT) {
+          gi = w % TI + 1; gj = (w / TI) % TJ + 1; gk = w / (TI * TJ) + 1;
+        } else if (w < NT + 2 * TJ * TK) {
+          const int s2 = w - NT, e = s2 % (TJ * TK);
+          gi = (s2 < TJ * TK) ? 0 : GI - 1; gj = e % TJ + 1; gk = e / TJ + 1;
+        } else if (w < NT + 2 * TJ * TK + 2 * TI * TK) {
+          const int s2 = w - NT - 2 * TJ * TK, e = s2 % (TI * TK);
+          gj = (s2 < TI * TK) ? 0 : GJ - 1; gi = e % TI + 1; gk = e / TI + 1;
+        } else {
+          const int s2 = w - NT - 2 * TJ * TK - 2 * TI * TK, e = s2 % (TI * TJ);
+          gk = (s2 < TI * TJ) ? 0 : GK - 1; gi = e % TI + 1; gj = e / TI + 1;
+        }
+        const int gq = (gk * GJ + gj) * GI + gi;
         const int r = rcell(gi + 1, gj + 1, gk + 1);
         const int i = i0 - 1 + gi, j = j0 - 1 + gj, k = k0 - 1 + gk;
         // ring cells beyond index n are never L or R of a computed face; their
