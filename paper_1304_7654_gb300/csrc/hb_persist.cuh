@@ -92,15 +92,20 @@ __global__ void __launch_bounds__(TI * TJ, (sizeof(T) == 4 ? 3 : 1) * (MAXNT / (
           halo_item<T, 2>(hp, g);
         if (!grid_barrier(P, nbar++)) return;
       }
+      // the next claim is issued when a tile starts and read when it ends,
+      // so the atomic's latency hides behind the tile's work
       unsigned int* ctr = P.work + it * 4 + s;
-      for (;;) {
-        if (threadIdx.x == 0) claim = (int)atomicAdd(ctr, 1u);
-        __syncthreads();
-        const int k = claim;
-        __syncthreads();
-        if (k >= P.ntiles) break;
+      if (threadIdx.x == 0) claim = (int)atomicAdd(ctr, 1u);
+      __syncthreads();
+      int k = claim;
+      while (k < P.ntiles) {
+        __syncthreads();   // every thread has read the claim
+        int next = 0;
+        if (threadIdx.x == 0) next = (int)atomicAdd(ctr, 1u);
         tile_any_ns<T, VISC, TI, TJ>(P.st[s], P.order[k], sm);
+        if (threadIdx.x == 0) claim = next;
         __syncthreads();
+        k = claim;
       }
       if (!grid_barrier(P, nbar++)) return;
       if (s == 0 && P.norms) {
