@@ -128,3 +128,52 @@ def test_full_size_box3d_sampled(prec):
     # local energy-flux scale: measured 1.9e-5, bounded by 5e-5
     assert err[:, :, :4].max() < 1e-5, err[:, :, :4].max()
     assert err[:, :, 4].max() < 5e-5, (err[:, :, 4].max(), tuple(cells[q]), n)
+
+
+def _batch3d():
+    return [C.box3d(12, 10, 8, n_harm=2, seed=21), C.box3d(9, 8, 5, n_harm=1, seed=22),
+            _split3d()]
+
+
+def test_batch_3d_trajectory_against_each_oracle():
+    """Three 3D cases (N_s 5, 3 and 5; one split into four blocks) advanced in
+    one context: every case's RK trajectory equals its own oracle run, so the
+    per-case slices of the stage workspace (the parked flux balances) do not
+    overlap."""
+    cases = _batch3d()
+    ctx = hb.HBContext(cases, "fp64")
+    Ug = ctx.new_state()
+    ctx.init_state(Ug, torch.as_tensor(np.concatenate([C.noise(c) for c in cases]), device="cuda"), 0.01)
+    ng = ctx.rk_smooth(Ug, 4).cpu().numpy()
+    assert ctx.sync_status() == hb.HB_OK
+    got = ctx.to_compact(Ug).cpu().numpy()
+    off = 0
+    for c, cs in enumerate(cases):
+        o = Oracle(cs)
+        Uo, no = o.rk_smooth(o.init_state(C.noise(cs), 0.01), 4)
+        ref = o.unpack(Uo)
+        part = got[off:off + ref.size]
+        off += ref.size
+        assert np.abs(part - ref).max() < 1e-12 * np.abs(ref).max(), c
+        assert np.allclose(ng[:, c, :cs.nv], no, rtol=1e-10), c
+
+
+def test_batch_3d_fp32_equals_each_case_alone():
+    """FP32: a case advanced inside the batch is bitwise the case advanced on
+    its own (the tile arithmetic does not depend on the other cases)."""
+    cases = _batch3d()
+    ctx = hb.HBContext(cases, "fp32")
+    Ug = ctx.new_state()
+    ctx.init_state(Ug, torch.as_tensor(np.concatenate([C.noise(c) for c in cases]), device="cuda"), 0.01)
+    ctx.rk_smooth(Ug, 6, norms=False)
+    got = ctx.to_compact(Ug).cpu()
+    off = 0
+    for cs in cases:
+        one = hb.HBContext(cs, "fp32")
+        U1 = one.new_state()
+        one.init_state(U1, torch.as_tensor(C.noise(cs), device="cuda"), 0.01)
+        one.rk_smooth(U1, 6, norms=False)
+        ref = one.to_compact(U1).cpu()
+        assert torch.equal(got[off:off + ref.numel()], ref.reshape(-1))
+        off += ref.numel()
+    assert ctx.sync_status() == hb.HB_OK
