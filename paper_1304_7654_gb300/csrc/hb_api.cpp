@@ -772,8 +772,12 @@ hb_status rebuild_tiles(hb_ctx* c, int TI, int TJ, int mode) {
     HB_CUDA(c, cudaMalloc(&c->d_partials, sizeof(double) * 8 * std::max(1, n)));
     c->max_tiles = n;
   }
-  if (c->dim == 3) {   // balance scratch of the RK stages: every tile's 256 cells x ns x nv
-    const size_t need = (size_t)std::max(1, n) * c->ns_max * c->nv * (8 * 8 * 4) * c->tsize;
+  // balance scratch of the RK stages: 3D tiles (256 cells x ns x nv each) and
+  // the persistent driver's 2D tiles (TI x TJ cells x the largest static N_s x nv)
+  if (c->dim == 3 || mode == 1) {
+    const size_t per_tile = (c->dim == 3) ? (size_t)c->ns_max * c->nv * (8 * 8 * 4)
+                                          : (size_t)(2 * HB_MAX_STATIC_HARMONICS + 1) * c->nv * TI * TJ;
+    const size_t need = (size_t)std::max(1, n) * per_tile * c->tsize;
     if (need > c->bal_bytes) {
       cudaFree(c->d_bal);
       c->d_bal = nullptr;
@@ -1392,6 +1396,7 @@ hb_status persist_chunk(hb_ctx* c, T* U, int K, cudaStream_t s) {
     p.st[st].Uprev = in[st];
     p.st[st].U0 = U;
     p.st[st].Unext = out[st];
+    p.st[st].R = (T*)c->d_bal;   // the tiles' parked balances
     p.st[st].alpha = (T)alpha[st];
     p.st[st].partials = (st == 0) ? c->d_partials : nullptr;
     if (c->fused()) {

@@ -139,7 +139,12 @@ struct Two<float> {
   using v = float2;
   static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
   static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-  static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+  // a - b as one packed fma: b * (-1) is exact, so the single rounding is that of a - b
+  static __device__ __forceinline__ float2 sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+  // c - h * x as one packed fma (h a power of two: h * x exact)
+  static __device__ __forceinline__ float2 fnma(float2 h, float2 x, float2 c) {
+    return __ffma2_rn(make_float2(-h.x, -h.y), x, c);
+  }
   static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
   static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
   static __device__ __forceinline__ float2 rcp(float2 a) {
@@ -156,6 +161,9 @@ struct Two<double> {
   static __device__ __forceinline__ double2 mul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
   static __device__ __forceinline__ double2 fma(double2 a, double2 b, double2 c) {
     return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y));
+  }
+  static __device__ __forceinline__ double2 fnma(double2 h, double2 x, double2 c) {
+    return make_double2(c.x - h.x * x.x, c.y - h.y * x.y);
   }
   static __device__ __forceinline__ double2 rcp(double2 a) {
     double2 r;
@@ -178,7 +186,7 @@ __device__ __forceinline__ void muscl2(typename Two<T>::v a, typename Two<T>::v 
   const auto sl = M::mul(M::fma(w1, d0, M::mul(w0, d1)), M::rcp(M::add(w0, w1)));
   const auto sr = M::mul(M::fma(w2, d1, M::mul(w1, d2)), M::rcp(M::add(w1, w2)));
   wl = M::fma(h, sl, b);
-  wr = M::sub(c, M::mul(h, sr));
+  wr = M::fnma(h, sr, c);
 }
 
 template <typename T>
@@ -294,9 +302,10 @@ constexpr int kMaxStaticNS = 9;
 
 // (NS = 0: the runtime snapshot count of the large-N_s path, whose HB
 // source comes precomputed, so it keeps no per-snapshot balances)
-__host__ __device__ constexpr size_t tile2d_smem_elems(int TI, int TJ, int NS, bool pipe) {
+// (balg: the per-snapshot balances are parked in global memory instead)
+__host__ __device__ constexpr size_t tile2d_smem_elems(int TI, int TJ, int NS, bool pipe, bool balg = false) {
   return (size_t)(pipe ? 15 : 10) * (TI + 4) * (TJ + 4) + (size_t)6 * (TI + 2) * (TJ + 2) +
-         (size_t)4 * ((TI + 1) * TJ + TI * (TJ + 1)) + (size_t)NS * 4 * TI * TJ + (size_t)NS * NS;
+         (size_t)4 * ((TI + 1) * TJ + TI * (TJ + 1)) + (size_t)(balg ? 0 : NS * 4 * TI * TJ) + (size_t)NS * NS;
 }
 
 // block-wide FP64 sum of up to 8 values, fixed order; result valid in thread 0
@@ -545,7 +554,10 @@ __global__ void __launch_bounds__(kSrcCells) td_source_kernel(const BlockDev* bl
 // from P.H and each snapshot is updated as soon as its face fluxes are known.
 // The tile shape TI x TJ (TI a power of two) is a compile-time constant so that
 // every flat-index decomposition is a multiply-shift.
-template <typename T, int NS, bool VISC, int MODE, int TI, int TJ, bool PIPE>
+// BALG: the per-snapshot flux balances of an RK stage wait for the epilogue in
+// this tile's slice of a global scratch (P.R, [tile][kMaxStaticNS][NV][NT])
+// instead of shared memory; the slice's L2 lines are discarded once read
+template <typename T, int NS, bool VISC, int MODE, int TI, int TJ, bool PIPE, bool BALG = false>
 __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   constexpr int NV = 4;
   const int4 tl = P.tiles[t];
@@ -575,7 +587,9 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   T* sG = sS + 4 * NR;     // [3][NG][2] gradients (x, y) of u, v, T on the 1-cell ring
   T* sF = sG + 6 * NG;     // [NV][NF] face fluxes
   T* sAcc = sF + 4 * NF;   // [NS][NV][NT] flux balance per snapshot of each own cell
-  T* sD = sAcc + NS * NV * NT;   // [NS][NS]
+  T* sD = sAcc + (BALG ? 0 : NS * NV * NT);   // [NS][NS]
+  static_assert(!BALG || (MODE == 1 && NS > 0 && NS <= kMaxStaticNS), "global balances: RK stages of static N_s");
+  T* const bal = BALG ? P.R + (int64_t)t * kMaxStaticNS * NV * NT : nullptr;
   constexpr bool DYN = NS == 0;
   const int ns = DYN ? C->ns : NS;
 
@@ -886,7 +900,10 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
         finish(n, Rn);
       } else {
 #pragma unroll
-        for (int q = 0; q < NV; ++q) sAcc[(n * NV + q) * NT + tid] = Rn[q];
+        for (int q = 0; q < NV; ++q) {
+          if constexpr (BALG) bal[(n * NV + q) * NT + tid] = Rn[q];
+          else sAcc[(n * NV + q) * NT + tid] = Rn[q];
+        }
       }
     }
   };
@@ -957,10 +974,21 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
           T h = T(0);
 #pragma unroll
           for (int m = 0; m < NS; ++m) h += sD[n * NS + m] * uu[m][q];
-          Rn[q] = sAcc[(n * NV + q) * NT + tid] + vw * h;
+          Rn[q] = (BALG ? bal[(n * NV + q) * NT + tid] : sAcc[(n * NV + q) * NT + tid]) + vw * h;
         }
         finish(n, Rn);
       }
+    }
+  }
+  if constexpr (BALG) {
+    // the parked balances are dead: drop their L2 lines unwritten (every lane
+    // of the warp has read its values before the barrier)
+    __syncwarp();
+    constexpr int LPP = (32 * (int)sizeof(T)) / 128;   // 128-byte lines per warp and (n, q)
+    const int lane = tid & 31;
+    for (int e = lane; e < NS * NV * LPP; e += 32) {
+      const T* line = bal + (e / LPP) * NT + (tid & ~31) + (e % LPP) * (128 / (int)sizeof(T));
+      asm volatile("discard.global.L2 [%0], 128;" ::"l"(line) : "memory");
     }
   }
 #pragma unroll
@@ -975,8 +1003,15 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   if (MODE == 1 && P.job_range) fill_tile_ghosts<T, NS>(P, t, B, C);
 }
 
+// CTAs per SM a tile kernel is compiled for: 24 warps in FP32, 8 in FP64;
+// the inviscid runtime-N_s tile of 128 threads (no balance array: 23 KB of
+// shared memory) runs eight CTAs (32 warps) within 64 registers, no spills
+__host__ __device__ constexpr int tile2d_min_ctas(bool fp32, int NS, bool VISC, int NT) {
+  return fp32 ? ((NS == 0 && !VISC && NT == 128) ? 8 : 3 * (MAXNT / NT)) : MAXNT / NT;
+}
+
 template <typename T, int NS, bool VISC, int MODE, int TI, int TJ>
-__global__ void __launch_bounds__(TI * TJ, (sizeof(T) == 4 ? 3 : 1) * (MAXNT / (TI * TJ)))
+__global__ void __launch_bounds__(TI * TJ, tile2d_min_ctas(sizeof(T) == 4, NS, VISC, TI * TJ))
     tile2d_kernel(StageParams<T> P) {
   extern __shared__ __align__(16) unsigned char smraw[];
   tile2d<T, NS, VISC, MODE, TI, TJ, tile_pipelined(NS)>(P, blockIdx.x, reinterpret_cast<T*>(smraw));

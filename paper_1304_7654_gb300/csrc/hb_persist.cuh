@@ -61,16 +61,17 @@ __device__ bool grid_barrier(const PersistParams<T>& P, int number) {
 }
 
 // the persistent driver serves cases of every snapshot count with one
-// shared-memory size, so its tiles run unpipelined (no second buffer)
+// shared-memory size: the tiles park their per-snapshot balances in global
+// memory (sp.R), which leaves room for the snapshot pipeline at any N_s
 template <typename T, bool VISC, int TI, int TJ>
 __device__ __forceinline__ void tile_any_ns(const StageParams<T>& sp, int t, T* sm) {
   const int ns = sp.cases[sp.blocks[sp.tiles[t].x].cs].ns;
   switch (ns) {
-    case 1: tile2d<T, 1, VISC, 1, TI, TJ, false>(sp, t, sm); break;
-    case 3: tile2d<T, 3, VISC, 1, TI, TJ, false>(sp, t, sm); break;
-    case 5: tile2d<T, 5, VISC, 1, TI, TJ, false>(sp, t, sm); break;
-    case 7: tile2d<T, 7, VISC, 1, TI, TJ, false>(sp, t, sm); break;
-    default: tile2d<T, 9, VISC, 1, TI, TJ, false>(sp, t, sm); break;
+    case 1: tile2d<T, 1, VISC, 1, TI, TJ, true, true>(sp, t, sm); break;
+    case 3: tile2d<T, 3, VISC, 1, TI, TJ, true, true>(sp, t, sm); break;
+    case 5: tile2d<T, 5, VISC, 1, TI, TJ, true, true>(sp, t, sm); break;
+    case 7: tile2d<T, 7, VISC, 1, TI, TJ, true, true>(sp, t, sm); break;
+    default: tile2d<T, 9, VISC, 1, TI, TJ, true, true>(sp, t, sm); break;
   }
 }
 
