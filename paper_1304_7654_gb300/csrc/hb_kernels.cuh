@@ -295,6 +295,9 @@ __device__ __forceinline__ void visc2d(const T* gL, const T* gR, T uL, T vL, T T
 // The snapshot loop of a tile is pipelined (primitives double-buffered)
 // where the extra shared memory keeps the occupancy: up to 7 snapshots.
 __host__ __device__ constexpr bool tile_pipelined(int NS) { return NS <= 7; }
+// An RK stage at the largest static N_s parks its per-snapshot balances in
+// global memory, which makes room for the pipeline there too
+__host__ __device__ constexpr bool tile_balg(int NS, int MODE) { return NS == 9 && MODE == 1; }
 
 // compile-time snapshot counts of the tile kernel; larger N_s run the
 // runtime-count instantiation (NS = 0)
@@ -1014,7 +1017,8 @@ template <typename T, int NS, bool VISC, int MODE, int TI, int TJ>
 __global__ void __launch_bounds__(TI * TJ, tile2d_min_ctas(sizeof(T) == 4, NS, VISC, TI * TJ))
     tile2d_kernel(StageParams<T> P) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  tile2d<T, NS, VISC, MODE, TI, TJ, tile_pipelined(NS)>(P, blockIdx.x, reinterpret_cast<T*>(smraw));
+  tile2d<T, NS, VISC, MODE, TI, TJ, tile_pipelined(NS) || tile_balg(NS, MODE), tile_balg(NS, MODE)>(
+      P, blockIdx.x, reinterpret_cast<T*>(smraw));
 }
 
 // tile shapes built into the library (index = StageParams shape id)
