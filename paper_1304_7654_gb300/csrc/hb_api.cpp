@@ -775,11 +775,11 @@ hb_status rebuild_tiles(hb_ctx* c, int TI, int TJ, int mode) {
   // balance scratch of the RK stages: 3D tiles (256 cells x ns x nv each) and
   // the 2D tiles of the persistent driver or of a case at the largest static
   // N_s (TI x TJ cells x that N_s x nv)
-  bool ns_top = false;
-  for (const auto& ch : c->cases) ns_top = ns_top || ch.ns == 2 * HB_MAX_STATIC_HARMONICS + 1;
-  if (c->dim == 3 || mode == 1 || ns_top) {
+  bool balg = false;
+  for (const auto& ch : c->cases) balg = balg || hbk::tile_balg(ch.ns, 1);
+  if (c->dim == 3 || mode == 1 || balg) {
     const size_t per_tile = (c->dim == 3) ? (size_t)c->ns_max * c->nv * (8 * 8 * 4)
-                                          : (size_t)(2 * HB_MAX_STATIC_HARMONICS + 1) * c->nv * TI * TJ;
+                                          : (size_t)hbk::kMaxStaticNS * c->nv * TI * TJ;
     const size_t need = (size_t)std::max(1, n) * per_tile * c->tsize;
     if (need > c->bal_bytes) {
       cudaFree(c->d_bal);
@@ -1255,9 +1255,11 @@ hb_status stage_all(hb_ctx* c, hbk::StageParams<T> p, int mode, cudaStream_t s) 
     TimedScope ts(c, 0, s);
     // the 3D tile parks each snapshot's flux balance in R until its epilogue
     if (c->dim == 3 && mode == 1) p.R = (T*)c->d_bal + (size_t)ch.tile0 * c->ns_max * c->nv * (8 * 8 * 4);
-    // (and so does a 2D tile at the largest static N_s)
-    if (c->dim == 2 && mode == 1 && ch.ns == 2 * HB_MAX_STATIC_HARMONICS + 1)
-      p.R = (T*)c->d_bal + (size_t)ch.tile0 * ch.ns * c->nv * c->TI * c->TJ;
+    // (and so does a 2D tile where tile_balg says so)
+    if (c->dim == 2 && hbk::tile_balg(ch.ns, mode)) {
+      if (!c->d_bal) return fail(c, HB_ERR_OOM, "stage: balance scratch not allocated");
+      p.R = (T*)c->d_bal + (size_t)ch.tile0 * hbk::kMaxStaticNS * c->nv * c->TI * c->TJ;
+    }
     if (c->dim == 3) HB_CUDA(c, hbk::launch_stage3d<T>(p, ch.ns, c->viscous, mode, s));
     else HB_CUDA(c, hbk::launch_stage<T>(p, ch.ns, c->viscous, mode, s));
     p.partials = part;

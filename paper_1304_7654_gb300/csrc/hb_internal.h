@@ -10,6 +10,14 @@ namespace hbk {
 
 constexpr int MAXNS = 31;      // 2 * HB_MAX_HARMONICS + 1
 constexpr int MAXNT = 256;     // threads per tile CTA
+// compile-time snapshot counts of the 2D tile kernel go up to this; larger
+// N_s run the runtime-count instantiation (NS = 0)
+constexpr int kMaxStaticNS = 9;
+// RK stages (MODE 1) whose 2D tile parks its per-snapshot flux balances in a
+// global scratch instead of shared memory: one slice of kMaxStaticNS x nv x
+// (TI x TJ) elements per tile, passed in StageParams::R by the host for
+// exactly these stages (the kernel and the host both ask this function)
+__host__ __device__ constexpr bool tile_balg(int NS, int MODE) { return NS == kMaxStaticNS && MODE == 1; }
 
 // Per-case constants, in the kernel precision T.  Frames and freestream are
 // tabulated per snapshot on the host in FP64 and rounded once.

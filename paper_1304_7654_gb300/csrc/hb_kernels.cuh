@@ -294,14 +294,10 @@ __device__ __forceinline__ void visc2d(const T* gL, const T* gR, T uL, T vL, T T
 // shared-memory elements of one tile CTA
 // The snapshot loop of a tile is pipelined (primitives double-buffered)
 // where the extra shared memory keeps the occupancy: up to 7 snapshots.
+// (an RK stage whose balances wait in global memory, tile_balg, has the room
+// for the pipeline at any static N_s)
 __host__ __device__ constexpr bool tile_pipelined(int NS) { return NS <= 7; }
-// An RK stage at the largest static N_s parks its per-snapshot balances in
-// global memory, which makes room for the pipeline there too
-__host__ __device__ constexpr bool tile_balg(int NS, int MODE) { return NS == 9 && MODE == 1; }
 
-// compile-time snapshot counts of the tile kernel; larger N_s run the
-// runtime-count instantiation (NS = 0)
-constexpr int kMaxStaticNS = 9;
 
 // (NS = 0: the runtime snapshot count of the large-N_s path, whose HB
 // source comes precomputed, so it keeps no per-snapshot balances)
@@ -593,6 +589,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   T* sD = sAcc + (BALG ? 0 : NS * NV * NT);   // [NS][NS]
   static_assert(!BALG || (MODE == 1 && NS > 0 && NS <= kMaxStaticNS), "global balances: RK stages of static N_s");
   T* const bal = BALG ? P.R + (int64_t)t * kMaxStaticNS * NV * NT : nullptr;
+  if (BALG && bal == nullptr) return;   // no scratch passed (the host refuses such a launch first)
   constexpr bool DYN = NS == 0;
   const int ns = DYN ? C->ns : NS;
 

@@ -75,8 +75,15 @@ __device__ __forceinline__ void tile_any_ns(const StageParams<T>& sp, int t, T* 
   }
 }
 
+// CTAs per SM the persistent kernel is compiled for: with its balances in
+// global memory a 128-thread tile needs ~24 KB of shared memory, and seven
+// FP32 CTAs (72 registers, a few spilled) outrun six (measured on the batch)
+__host__ __device__ constexpr int persist_min_ctas(bool fp32, int NT) {
+  return fp32 ? (NT == 128 ? 7 : 3 * (MAXNT / NT)) : MAXNT / NT;
+}
+
 template <typename T, bool VISC, int TI, int TJ>
-__global__ void __launch_bounds__(TI * TJ, (sizeof(T) == 4 ? 3 : 1) * (MAXNT / (TI * TJ)))
+__global__ void __launch_bounds__(TI * TJ, persist_min_ctas(sizeof(T) == 4, TI * TJ))
     persist_kernel(PersistParams<T> P) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
