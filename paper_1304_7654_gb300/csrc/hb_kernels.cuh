@@ -173,6 +173,12 @@ struct Two<double> {
   static __device__ __forceinline__ double2 ld(const double* p) { return *reinterpret_cast<const double2*>(p); }
 };
 
+// an int index descriptor carried in a slot of a floating-point record
+__device__ __forceinline__ float int_in(float, int v) { return __int_as_float(v); }
+__device__ __forceinline__ double int_in(double, int v) { return (double)v; }
+__device__ __forceinline__ int int_of(float x) { return __float_as_int(x); }
+__device__ __forceinline__ int int_of(double x) { return (int)x; }
+
 // MUSCL face states of two variables at once from the stencil a | b || c | d
 // (face between b and c): WL = b + va(b-a, c-b)/2, WR = c - va(c-b, d-c)/2
 template <typename T>
@@ -294,17 +300,23 @@ __device__ __forceinline__ void visc2d(const T* gL, const T* gR, T uL, T vL, T T
 // shared-memory elements of one tile CTA
 // The snapshot loop of a tile is pipelined (primitives double-buffered)
 // where the extra shared memory keeps the occupancy: up to 7 snapshots.
-// (an RK stage whose balances wait in global memory, tile_balg, has the room
-// for the pipeline at any static N_s)
-__host__ __device__ constexpr bool tile_pipelined(int NS) { return NS <= 7; }
+// A tile whose per-snapshot balances wait in global memory (tile_park) has
+// the room for the pipeline at any static N_s: an RK stage where tile_balg
+// says so (a scratch slice per tile), and every residual evaluation (the
+// residual output itself holds them until the epilogue adds the HB source)
+__host__ __device__ constexpr bool tile_park(int NS, int MODE) { return tile_balg(NS, MODE) || (MODE == 0 && NS > 0); }
+__host__ __device__ constexpr bool tile_pipelined(int NS, int MODE) { return NS <= 7 || tile_park(NS, MODE); }
 
 
 // (NS = 0: the runtime snapshot count of the large-N_s path, whose HB
 // source comes precomputed, so it keeps no per-snapshot balances)
 // (balg: the per-snapshot balances are parked in global memory instead)
-__host__ __device__ constexpr size_t tile2d_smem_elems(int TI, int TJ, int NS, bool pipe, bool balg = false) {
+// (face records of tile2d_face_words elements per face work item)
+__host__ __device__ constexpr int tile2d_face_words(bool visc) { return visc ? 4 : 2; }
+__host__ __device__ constexpr size_t tile2d_smem_elems(int TI, int TJ, int NS, bool pipe, bool balg, bool visc) {
   return (size_t)(pipe ? 15 : 10) * (TI + 4) * (TJ + 4) + (size_t)6 * (TI + 2) * (TJ + 2) +
-         (size_t)4 * ((TI + 1) * TJ + TI * (TJ + 1)) + (size_t)(balg ? 0 : NS * 4 * TI * TJ) + (size_t)NS * NS;
+         (size_t)(4 + tile2d_face_words(visc)) * ((TI + 1) * TJ + TI * (TJ + 1)) +
+         (size_t)(balg ? 0 : NS * 4 * TI * TJ) + (size_t)NS * NS;
 }
 
 // block-wide FP64 sum of up to 8 values, fixed order; result valid in thread 0
@@ -553,9 +565,10 @@ __global__ void __launch_bounds__(kSrcCells) td_source_kernel(const BlockDev* bl
 // from P.H and each snapshot is updated as soon as its face fluxes are known.
 // The tile shape TI x TJ (TI a power of two) is a compile-time constant so that
 // every flat-index decomposition is a multiply-shift.
-// BALG: the per-snapshot flux balances of an RK stage wait for the epilogue in
-// this tile's slice of a global scratch (P.R, [tile][kMaxStaticNS][NV][NT])
-// instead of shared memory; the slice's L2 lines are discarded once read
+// BALG: the per-snapshot flux balances wait for the epilogue in global memory
+// instead of shared memory: in an RK stage in this tile's slice of a scratch
+// (P.R, [tile][kMaxStaticNS][NV][NT]), whose L2 lines are discarded once read;
+// in a residual evaluation in the residual output P.R itself
 template <typename T, int NS, bool VISC, int MODE, int TI, int TJ, bool PIPE, bool BALG = false>
 __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   constexpr int NV = 4;
@@ -586,10 +599,13 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   T* sG = sS + 4 * NR;     // [3][NG][2] gradients (x, y) of u, v, T on the 1-cell ring
   T* sF = sG + 6 * NG;     // [NV][NF] face fluxes
   T* sAcc = sF + 4 * NF;   // [NS][NV][NT] flux balance per snapshot of each own cell
-  T* sD = sAcc + (BALG ? 0 : NS * NV * NT);   // [NS][NS]
-  static_assert(!BALG || (MODE == 1 && NS > 0 && NS <= kMaxStaticNS), "global balances: RK stages of static N_s");
-  T* const bal = BALG ? P.R + (int64_t)t * kMaxStaticNS * NV * NT : nullptr;
-  if (BALG && bal == nullptr) return;   // no scratch passed (the host refuses such a launch first)
+  constexpr int FRW = tile2d_face_words(VISC);
+  T* sFR = sAcc + (BALG ? 0 : NS * NV * NT);   // [NF][FRW] per face work item: (vg, dcx, dcy, descriptor), or (vg, descriptor) inviscid
+  T* sD = sFR + FRW * NF;   // [NS][NS]
+  static_assert(RI * (TJ + 4) <= 512 && NF <= 1024 && GI * (TJ + 2) <= 512, "face descriptor fields");
+  static_assert(!BALG || (NS > 0 && NS <= kMaxStaticNS), "global balances: static N_s");
+  T* const bal = (BALG && MODE == 1) ? P.R + (int64_t)t * kMaxStaticNS * NV * NT : nullptr;
+  if (BALG && P.R == nullptr) return;   // no scratch passed (the host refuses such a launch first)
   constexpr bool DYN = NS == 0;
   const int ns = DYN ? C->ns : NS;
 
@@ -637,6 +653,51 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
     }
   }
   for (int e = tid; e < NS * NS; e += nt) sD[e] = C->D[e];
+  // the face work items, decoded once per stage (they are the same for every
+  // snapshot): work item w -> bit 0 used, bit 1 direction d, bits 2-10 region
+  // index of L, bits 11-20 flux storage index, bits 21-29 ring index of L;
+  // with the static grid-velocity factor and centre difference of the face.
+  // Order of w: the first TI x TJ i-faces row by row, TI to a row (a warp
+  // reads one region row: no bank conflicts), then the TJ faces of column TI,
+  // then the j-faces
+  for (int w = tid; w < NF; w += nt) {
+    int d, fi, fj, fq, rL, gLi;
+    bool used;
+    if (w < NFI) {
+      if (w < TI * TJ) {
+        fi = w % TI;
+        fj = w / TI;
+      } else {
+        fi = TI;
+        fj = w - TI * TJ;
+      }
+      fq = fj * (TI + 1) + fi;
+      used = !(i0 + fi > n0 || j0 + fj >= je);
+      rL = (fj + 2) * RI + (fi + 1);
+      d = 0;
+      gLi = (fj + 1) * GI + fi;
+    } else {
+      const int g2 = w - NFI;
+      fi = g2 % TI;
+      fj = g2 / TI;
+      fq = w;
+      used = !(i0 + fi >= n0 || j0 + fj > je);
+      rL = (fj + 1) * RI + (fi + 2);
+      d = 1;
+      gLi = fj * GI + fi + 1;
+    }
+    // the face is the low face of cell R = (i0 + fi, j0 + fj) along d
+    const int64_t gR = B.goff + (int64_t)(j0 + fj + 2) * P0 + (i0 + fi + 2);
+    const T vg = (used && moving) ? P.g.q[G_VG + d][gR] : T(0);
+    const int desc = (used ? 1 : 0) | (d << 1) | (rL << 2) | (fq << 11) | (gLi << 21);
+    if constexpr (VISC) {
+      const T dx = used ? P.g.q[G_DC + 3 * d][gR] : T(1);
+      const T dy = used ? P.g.q[G_DC + 3 * d + 1][gR] : T(0);
+      sts4(sFR + 4 * w, vg, dx, dy, int_in(T(0), desc));
+    } else {
+      sts2(sFR + 2 * w, vg, int_in(T(0), desc));
+    }
+  }
 
   const int ti = tid % TI, tj = tid / TI;
   const int ci = i0 + ti, cj = j0 + tj;
@@ -749,36 +810,15 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   auto face = [&](int w, const Fr<T>& f, int b) {
     const T* W = sW + b * 4 * NR;
     const T* TT = sT + b * NR;
-    int rL, st, d, gLi, gRi, fi, fj, fq = w;
-    if (w < NFI) {
-      if (w < TI * TJ) {
-        fi = w % TI;
-        fj = w / TI;
-      } else {
-        fi = TI;
-        fj = w - TI * TJ;
-      }
-      fq = fj * (TI + 1) + fi;
-      if (i0 + fi > n0 || j0 + fj >= je) return;
-      rL = (fj + 2) * RI + (fi + 1);
-      st = 1;
-      d = 0;
-      gLi = (fj + 1) * GI + fi;
-      gRi = gLi + 1;
-    } else {
-      const int g2 = fq - NFI;
-      fi = g2 % TI;
-      fj = g2 / TI;
-      if (i0 + fi >= n0 || j0 + fj > je) return;
-      rL = (fj + 1) * RI + (fi + 2);
-      st = RI;
-      d = 1;
-      gLi = fj * GI + fi + 1;
-      gRi = gLi + GI;
-    }
+    T vgf, dcx = T(1), dcy = T(0), dsc;
+    if constexpr (VISC) lds4(sFR + 4 * w, vgf, dcx, dcy, dsc);
+    else lds2(sFR + 2 * w, vgf, dsc);
+    const int desc = int_of(dsc);
+    if (!(desc & 1)) return;
+    const int d = (desc >> 1) & 1, rL = (desc >> 2) & 511, fq = (desc >> 11) & 1023, gLi = (desc >> 21) & 511;
+    const int st = d ? RI : 1;
+    const int gRi = gLi + (d ? GI : 1);
     const int rR = rL + st;
-    // the face is the low face of cell R = (i0 + fi, j0 + fj) along d
-    const int64_t gR = B.goff + (int64_t)(j0 + fj + 2) * P0 + (i0 + fi + 2);
     // the four cells of the stencil, (u, v) and (rho, p) of each, limited
     // two variables at a time
     using M = Two<T>;
@@ -794,7 +834,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
     T sx, sy;
     rotv(f, sS[(2 * d) * NR + rR], sS[(2 * d + 1) * NR + rR], sx, sy);
     // normal grid velocity of the pitching face: thdot times its static factor
-    const T vgn = moving ? f.thd * __ldg(P.g.q[G_VG + d] + gR) : T(0);
+    const T vgn = moving ? f.thd * vgf : T(0);
     T F[4];
     roe2d(WL, WR, sx, sy, vgn, gm1, gg1, efix, efrac, hef, F);
     if (VISC) {
@@ -805,7 +845,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
         lds2(sG + 2 * (q * NG + gRi), gr[2 * q], gr[2 * q + 1]);
       }
       T tx, ty;
-      rotv(f, __ldg(P.g.q[G_DC + 3 * d] + gR), __ldg(P.g.q[G_DC + 3 * d + 1] + gR), tx, ty);
+      rotv(f, dcx, dcy, tx, ty);
       T Fv[4];
       visc2d(gl, gr, uvb.x, uvb.y, TT[rL], uvc.x, uvc.y, TT[rR], tx, ty, sx,
              sy, mu, kap, Fv);
@@ -901,7 +941,8 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
       } else {
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
-          if constexpr (BALG) bal[(n * NV + q) * NT + tid] = Rn[q];
+          if constexpr (BALG && MODE == 1) bal[(n * NV + q) * NT + tid] = Rn[q];
+          else if constexpr (BALG) P.R[B.off + ((int64_t)n * NV + q) * B.plane + cown] = Rn[q];
           else sAcc[(n * NV + q) * NT + tid] = Rn[q];
         }
       }
@@ -974,13 +1015,17 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
           T h = T(0);
 #pragma unroll
           for (int m = 0; m < NS; ++m) h += sD[n * NS + m] * uu[m][q];
-          Rn[q] = (BALG ? bal[(n * NV + q) * NT + tid] : sAcc[(n * NV + q) * NT + tid]) + vw * h;
+          T bq;
+          if constexpr (BALG && MODE == 1) bq = bal[(n * NV + q) * NT + tid];
+          else if constexpr (BALG) bq = P.R[B.off + ((int64_t)n * NV + q) * B.plane + cown];
+          else bq = sAcc[(n * NV + q) * NT + tid];
+          Rn[q] = bq + vw * h;
         }
         finish(n, Rn);
       }
     }
   }
-  if constexpr (BALG) {
+  if constexpr (BALG && MODE == 1) {
     // the parked balances are dead: drop their L2 lines unwritten (every lane
     // of the warp has read its values before the barrier)
     __syncwarp();
@@ -1004,17 +1049,18 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
 }
 
 // CTAs per SM a tile kernel is compiled for: 24 warps in FP32, 8 in FP64;
-// the inviscid runtime-N_s tile of 128 threads (no balance array: 23 KB of
-// shared memory) runs eight CTAs (32 warps) within 64 registers, no spills
+// the inviscid runtime-N_s tile of 128 threads (no balance array: 25 KB of
+// shared memory) runs seven CTAs (28 warps) within 72 registers (eight
+// spilled and measured slower)
 __host__ __device__ constexpr int tile2d_min_ctas(bool fp32, int NS, bool VISC, int NT) {
-  return fp32 ? ((NS == 0 && !VISC && NT == 128) ? 8 : 3 * (MAXNT / NT)) : MAXNT / NT;
+  return fp32 ? ((NS == 0 && !VISC && NT == 128) ? 7 : 3 * (MAXNT / NT)) : MAXNT / NT;
 }
 
 template <typename T, int NS, bool VISC, int MODE, int TI, int TJ>
 __global__ void __launch_bounds__(TI * TJ, tile2d_min_ctas(sizeof(T) == 4, NS, VISC, TI * TJ))
     tile2d_kernel(StageParams<T> P) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  tile2d<T, NS, VISC, MODE, TI, TJ, tile_pipelined(NS) || tile_balg(NS, MODE), tile_balg(NS, MODE)>(
+  tile2d<T, NS, VISC, MODE, TI, TJ, tile_pipelined(NS, MODE), tile_park(NS, MODE)>(
       P, blockIdx.x, reinterpret_cast<T*>(smraw));
 }
 
