@@ -140,7 +140,11 @@ typedef struct {
 typedef struct hb_ctx hb_ctx;   /* opaque, library-owned */
 
 /* Create a context: validates and copies the descriptors, uploads geometry,
- * allocates library-owned workspace on the current CUDA device.  Errors:
+ * allocates library-owned workspace on the current CUDA device (two RK stage
+ * buffers of the state's size, the precomputed metrics, and for 3D cases,
+ * N_s 7 and 9 cases and the persistent driver a per-tile scratch of about the
+ * state's size that holds each tile's per-snapshot flux balances during an RK
+ * stage; hb_set_tuning and hb_autotune may grow it).  Errors:
  * HB_ERR_INVALID_ARG for malformed tables (cut boxes outside the ghost
  * layers, sources outside the allowed range, unknown BC types, block ids out
  * of range), HB_ERR_UNSUPPORTED for N_H > HB_MAX_HARMONICS, HB_ERR_OOM. */
