@@ -71,6 +71,28 @@ def test_batch_equals_cases_run_alone(prec):
                 assert (a_ - b_).abs().max() <= 2e-6 * b_.abs().max(), (k, (a_ - b_).abs().max())
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_per_phase_batch_equals_cases_run_alone(prec):
+    """Per-phase launches (one per case and stage): each case of the batch is
+    bitwise the case advanced alone with the same driver and tile shape, also
+    the N_s = 7 and 9 cases whose tiles park their balances in per-case slices
+    of the stage scratch (the slices of different cases do not overlap)."""
+    cases = _small_batch(8, seed=20)
+    assert {7, 9} <= {c.n_snap for c in cases}
+    bctx = hb.HBContext(cases, prec)
+    bctx.set_tuning(0, 32, 8)
+    Ub = _batch_state(bctx, cases)
+    bctx.rk_smooth(Ub, 3, norms=False)
+    assert bctx.sync_status() == hb.HB_OK
+    for k, (c, (a, e)) in enumerate(zip(cases, _case_slices(bctx, cases))):
+        ctx = hb.HBContext(c, prec)
+        ctx.set_tuning(0, 32, 8)
+        U = ctx.new_state()
+        ctx.init_state(U, torch.as_tensor(C.noise(c), device="cuda"), 0.01)
+        ctx.rk_smooth(U, 3, norms=False)
+        assert torch.equal(ctx.to_compact(U), ctx.to_compact(Ub[a:e].clone())), (k, c.n_snap)
+
+
 def test_batch_fp64_matches_oracle_per_case():
     cases = _small_batch(4, seed=19)
     bctx = hb.HBContext(cases, "fp64")
