@@ -112,7 +112,7 @@ typedef struct {
  * p_inf = 1/gamma, |u_inf| = mach, mu = mach/reynolds (constant),
  * heat conductivity mu/((gamma-1) prandtl), reference length 1. */
 typedef struct {
-  int dim;                    /* 2 or 3; 3D runs one launch per phase with 8x8x4 tiles and has no
+  int dim;                    /* 2 or 3; 3D runs one launch per phase with 8x8x8 (FP32) or 8x8x4 (FP64) tiles and has no
                                  force integration or adjoint (HB_ERR_UNSUPPORTED) */
   int n_harm;                 /* N_H, 0 .. HB_MAX_HARMONICS (3D: .. HB_MAX_STATIC_HARMONICS) */
   double mach, reynolds, prandtl, gamma;

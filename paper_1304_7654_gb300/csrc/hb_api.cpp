@@ -705,7 +705,8 @@ hb_status rebuild_tiles(hb_ctx* c, int TI, int TJ, int mode) {
   auto cells_of = [&](const int4& t) -> long long {
     const BlockDev& B = c->blocks[t.x];
     if (c->dim == 3)
-      return (long long)std::min(8, B.n[0] - t.y) * std::min(8, B.n[1] - t.z) * std::min(4, B.n[2] - t.w);
+      return (long long)std::min(8, B.n[0] - t.y) * std::min(8, B.n[1] - t.z) *
+             std::min(hbk::tile3d_tk(c->prec == HB_FP32), B.n[2] - t.w);
     return (long long)std::min(TI, B.n[0] - t.y) * t.w;
   };
   for (size_t k = 0; k < c->cases.size(); ++k) {
@@ -714,8 +715,8 @@ hb_status rebuild_tiles(hb_ctx* c, int TI, int TJ, int mode) {
     std::vector<int4> ct;
     for (int b = 0; b < ch.nblocks; ++b) {
       const BlockDev& B = c->blocks[ch.block0 + b];
-      if (c->dim == 3) {   // fixed 8 x 8 x 4 tiles
-        for (int k = 0; k < B.n[2]; k += 4)
+      if (c->dim == 3) {   // fixed 8 x 8 x tk tiles
+        for (int k = 0; k < B.n[2]; k += hbk::tile3d_tk(c->prec == HB_FP32))
           for (int j = 0; j < B.n[1]; j += 8)
             for (int i = 0; i < B.n[0]; i += 8) ct.push_back(make_int4(ch.block0 + b, i, j, k));
         continue;
@@ -778,7 +779,7 @@ hb_status rebuild_tiles(hb_ctx* c, int TI, int TJ, int mode) {
   bool balg = false;
   for (const auto& ch : c->cases) balg = balg || hbk::tile_balg(ch.ns, 1);
   if (c->dim == 3 || mode == 1 || balg) {
-    const size_t per_tile = (c->dim == 3) ? (size_t)c->ns_max * c->nv * (8 * 8 * 4)
+    const size_t per_tile = (c->dim == 3) ? (size_t)c->ns_max * c->nv * (8 * 8 * hbk::tile3d_tk(c->prec == HB_FP32))
                                           : (size_t)hbk::kMaxStaticNS * c->nv * TI * TJ;
     const size_t need = (size_t)std::max(1, n) * per_tile * c->tsize;
     if (need > c->bal_bytes) {
@@ -1254,7 +1255,8 @@ hb_status stage_all(hb_ctx* c, hbk::StageParams<T> p, int mode, cudaStream_t s) 
     if (p.lam_v == T(0) && ch.ns <= 2 * HB_MAX_STATIC_HARMONICS + 1) p.H = nullptr;
     TimedScope ts(c, 0, s);
     // the 3D tile parks each snapshot's flux balance in R until its epilogue
-    if (c->dim == 3 && mode == 1) p.R = (T*)c->d_bal + (size_t)ch.tile0 * c->ns_max * c->nv * (8 * 8 * 4);
+    if (c->dim == 3 && mode == 1)
+      p.R = (T*)c->d_bal + (size_t)ch.tile0 * c->ns_max * c->nv * (8 * 8 * hbk::tile3d_tk(sizeof(T) == 4));
     // (and so does a 2D tile where tile_balg says so)
     if (c->dim == 2 && hbk::tile_balg(ch.ns, mode)) {
       if (!c->d_bal) return fail(c, HB_ERR_OOM, "stage: balance scratch not allocated");
@@ -2020,7 +2022,7 @@ hb_status hb_set_tuning(hb_ctx* ctx, int mode, int TI, int TJ) {
   if (!ctx || mode < 0 || mode > 3) return fail(ctx, HB_ERR_INVALID_ARG, "bad tuning");
   const bool phases = (mode & 2) != 0;
   mode &= 1;
-  if (ctx->dim == 3) return fail(ctx, HB_ERR_UNSUPPORTED, "3D contexts use fixed 8x8x4 tiles, one launch per phase");
+  if (ctx->dim == 3) return fail(ctx, HB_ERR_UNSUPPORTED, "3D contexts use fixed 8x8x8 (FP32) or 8x8x4 (FP64) tiles, one launch per phase");
   const bool ok = (TI == 32 && TJ == 8) || (TI == 32 && TJ == 4) || (TI == 16 && TJ == 8);
   if (!ok) return fail(ctx, HB_ERR_UNSUPPORTED, "tile shape not built");
   const bool pok = ctx->prec == HB_FP32 ? hbk::persist_available<float>(TI, TJ)

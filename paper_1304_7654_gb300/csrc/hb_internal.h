@@ -19,6 +19,10 @@ constexpr int kMaxStaticNS = 9;
 // exactly these stages (the kernel and the host both ask this function).
 // At N_s = 9 this makes room for the snapshot pipeline; at N_s = 7 the tile
 // measured slightly faster with the balances in L2 than in shared memory.
+// k depth of a 3D tile (8 x 8 x tk cells, one thread per cell): 8 in FP32
+// (512 threads, one CTA per SM, less halo work per cell: measured faster),
+// 4 in FP64 (two 256-thread CTAs would not fit its registers at 512)
+__host__ __device__ constexpr int tile3d_tk(bool fp32) { return fp32 ? 8 : 4; }
 __host__ __device__ constexpr bool tile_balg(int NS, int MODE) { return (NS == kMaxStaticNS || NS == 7) && MODE == 1; }
 
 // Per-case constants, in the kernel precision T.  Frames and freestream are

@@ -2,7 +2,8 @@
 // 2D kernel (hb_kernels.cuh) with five conservative variables, three face
 // directions and the full 3x3 Stokes stress.
 //
-// One CTA owns an 8 x 8 x 4 tile of one block and loops over all snapshots.
+// One CTA owns an 8 x 8 x 8 (FP32) or 8 x 8 x 4 (FP64) tile of one block and
+// loops over all snapshots.
 // Once per stage it stages the static geometry in shared memory: 1/V of the
 // region, the low-face vectors of every face the gradient ring and the tile
 // close over, and the centre differences of the tile's faces.  Per snapshot
@@ -18,7 +19,7 @@
 
 namespace hbk {
 
-constexpr int T3I = 8, T3J = 8, T3K = 4;
+constexpr int T3I = 8, T3J = 8;
 
 // Roe flux of the 3D path, written as roe2d with a third velocity component
 template <typename T>
@@ -118,31 +119,36 @@ __device__ __forceinline__ void visc3d(const T* gL, const T* gR, const T* pL, co
           kap * (g[9] * Sx + g[10] * Sy + g[11] * Sz);
 }
 
-// region (tile + 2-cell halo), gradient ring (tile + 1 cell), faces of the tile
-constexpr int R3I = T3I + 4, R3J = T3J + 4, R3K = T3K + 4, NR3 = R3I * R3J * R3K;
-constexpr int G3I = T3I + 2, G3J = T3J + 2, G3K = T3K + 2, NG3 = G3I * G3J * G3K;
-constexpr int NF3I = (T3I + 1) * T3J * T3K, NF3J = T3I * (T3J + 1) * T3K, NF3K = T3I * T3J * (T3K + 1);
-constexpr int NF3 = NF3I + NF3J + NF3K;
+// region (tile + 2-cell halo), gradient ring (tile + 1 cell), faces of the
+// tile; tk the tile's k depth (tile3d_tk)
+constexpr int R3I = T3I + 4, R3J = T3J + 4;
+constexpr int G3I = T3I + 2, G3J = T3J + 2;
+__host__ __device__ constexpr int nr3(int tk) { return R3I * R3J * (tk + 4); }
+__host__ __device__ constexpr int ng3(int tk) { return G3I * G3J * (tk + 2); }
+__host__ __device__ constexpr int nf3(int tk) { return (T3I + 1) * T3J * tk + T3I * (T3J + 1) * tk + T3I * T3J * (tk + 1); }
 // low-face vectors along d of the ring box extended by one cell on the high
 // side along d: every face a ring cell closes over, and every face of the tile
 __host__ __device__ constexpr int sbox3_i(int d) { return G3I + (d == 0); }
 __host__ __device__ constexpr int sbox3_j(int d) { return G3J + (d == 1); }
-__host__ __device__ constexpr int sbox3_n(int d) { return sbox3_i(d) * sbox3_j(d) * (G3K + (d == 2)); }
-__host__ __device__ constexpr int sbox3_off(int d) { return d == 0 ? 0 : (d == 1 ? 3 * sbox3_n(0) : 3 * (sbox3_n(0) + sbox3_n(1))); }
-constexpr int NSB3 = 3 * (sbox3_n(0) + sbox3_n(1) + sbox3_n(2));
+__host__ __device__ constexpr int sbox3_n(int d, int tk) { return sbox3_i(d) * sbox3_j(d) * (tk + 2 + (d == 2)); }
+__host__ __device__ constexpr int sbox3_off(int d, int tk) {
+  return d == 0 ? 0 : (d == 1 ? 3 * sbox3_n(0, tk) : 3 * (sbox3_n(0, tk) + sbox3_n(1, tk)));
+}
+__host__ __device__ constexpr int nsb3(int tk) { return 3 * (sbox3_n(0, tk) + sbox3_n(1, tk) + sbox3_n(2, tk)); }
 
-__host__ __device__ constexpr size_t tile3d_smem_elems(int NS) {
-  return (size_t)7 * NR3 + (size_t)12 * NG3 + (size_t)5 * NF3 + (size_t)NSB3 + (size_t)3 * NF3 + (size_t)NS * NS;
+__host__ __device__ constexpr size_t tile3d_smem_elems(int NS, int tk) {
+  return (size_t)7 * nr3(tk) + (size_t)12 * ng3(tk) + (size_t)5 * nf3(tk) + (size_t)nsb3(tk) + (size_t)3 * nf3(tk) +
+         (size_t)NS * NS;
 }
 
 template <typename T, int NS, bool VISC, int MODE>
 __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
   constexpr int NV = 5;
-  constexpr int TI = T3I, TJ = T3J, TK = T3K, NT = TI * TJ * TK;
-  constexpr int RI = R3I, RJ = R3J, NR = NR3;
-  constexpr int GI = G3I, GJ = G3J, GK = G3K, NG = NG3;
+  constexpr int TI = T3I, TJ = T3J, TK = tile3d_tk(sizeof(T) == 4), NT = TI * TJ * TK;
+  constexpr int RI = R3I, RJ = R3J, R3K = TK + 4, NR = nr3(TK);
+  constexpr int GI = G3I, GJ = G3J, GK = TK + 2, NG = ng3(TK);
   constexpr int NGU = TI * TJ * TK + 2 * (TJ * TK + TI * TK + TI * TJ);
-  constexpr int NFI = NF3I, NFJ = NF3J, NF = NF3;
+  constexpr int NFI = (TI + 1) * TJ * TK, NFJ = TI * (TJ + 1) * TK, NF = nf3(TK);
   const int4 tl = P.tiles[t];
   const BlockDev B = P.blocks[tl.x];
   const CaseDev<T>* C = P.cases + B.cs;
@@ -158,7 +164,7 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
   T* sG = sIV + NR;        // [NG][12] gradients of (u, v, w, T), (x, y, z) each, ring box order
   T* sF = sG + 12 * NG;    // [NV][NF]
   T* sSb = sF + NV * NF;   // [d][3][box of d] static low-face vectors
-  T* sDC = sSb + NSB3;     // [3][NF] static centre differences of the tile's faces
+  T* sDC = sSb + nsb3(TK);     // [3][NF] static centre differences of the tile's faces
   T* sD = sDC + 3 * NF;    // [NS][NS]
 
   const T gam = C->gamma, gm1 = C->gamma - T(1), eps = C->eps, efrac = C->ent_frac;
@@ -187,7 +193,7 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
   // (every load of a thread issued before the first is used; blockDim.x = NT)
   {
     constexpr int ITR = (NR + NT - 1) / NT;
-    constexpr int ITS = (sbox3_n(2) + NT - 1) / NT;   // the largest of the three boxes
+    constexpr int ITS = (sbox3_n(2, TK) + NT - 1) / NT;   // the largest of the three boxes
     T vq[ITR], sq[3][ITS][3];
 #pragma unroll
     for (int it = 0; it < ITR; ++it) {
@@ -204,7 +210,7 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
         const int EI = sbox3_i(d), EJ = sbox3_j(d);
         const int gi = e % EI, gj = (e / EI) % EJ, gk = e / (EI * EJ);
         const int i = i0 - 1 + gi, j = j0 - 1 + gj, k = k0 - 1 + gk;
-        const bool in = e < sbox3_n(d) && inpad(i, j, k);
+        const bool in = e < sbox3_n(d, TK) && inpad(i, j, k);
         const int64_t c = B.goff + pcell(i, j, k);
 #pragma unroll
         for (int a = 0; a < 3; ++a) sq[d][it][a] = in ? P.g.q[G_S + 3 * d + a][c] : T(0);
@@ -217,9 +223,9 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
 #pragma unroll
       for (int it = 0; it < ITS; ++it) {
         const int e = tid + it * NT;
-        if (e < sbox3_n(d))
+        if (e < sbox3_n(d, TK))
 #pragma unroll
-          for (int a = 0; a < 3; ++a) sSb[sbox3_off(d) + a * sbox3_n(d) + e] = sq[d][it][a];
+          for (int a = 0; a < 3; ++a) sSb[sbox3_off(d, TK) + a * sbox3_n(d, TK) + e] = sq[d][it][a];
       }
   }
   if (VISC) {
@@ -334,8 +340,8 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
         const int rs[3] = {1, RI, RI * RJ};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          const T* Sd = sSb + sbox3_off(d);
-          const int NB = sbox3_n(d);
+          const T* Sd = sSb + sbox3_off(d, TK);
+          const int NB = sbox3_n(d, TK);
           const int lo = sbidx(d, gi, gj, gk);
           const int hi = lo + (d == 0 ? 1 : (d == 1 ? sbox3_i(1) : sbox3_i(2) * sbox3_j(2)));
 #pragma unroll
@@ -395,8 +401,8 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
         rhoR = c - T(0.5) * van_albada_w(d1, d2, w1, va_weight(d2, eps));
       }
       const T WL[5] = {rhoL, uvL.x, uvL.y, wpL.x, wpL.y}, WR[5] = {rhoR, uvR.x, uvR.y, wpR.x, wpR.y};
-      const T* Sd = sSb + sbox3_off(d);
-      const int NB = (d == 0) ? sbox3_n(0) : (d == 1 ? sbox3_n(1) : sbox3_n(2));
+      const T* Sd = sSb + sbox3_off(d, TK);
+      const int NB = (d == 0) ? sbox3_n(0, TK) : (d == 1 ? sbox3_n(1, TK) : sbox3_n(2, TK));
       const int eR = (d == 0) ? sbidx(0, fi + 1, fj + 1, fk + 1)
                               : (d == 1 ? sbidx(1, fi + 1, fj + 1, fk + 1) : sbidx(2, fi + 1, fj + 1, fk + 1));
       T sx, sy;
@@ -467,8 +473,8 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
     T Sb[3][3], m2[3], mg[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const T* Sd = sSb + sbox3_off(d);
-      const int NB = sbox3_n(d);
+      const T* Sd = sSb + sbox3_off(d, TK);
+      const int NB = sbox3_n(d, TK);
       const int lo = sbidx(d, ti + 1, tj + 1, tk + 1);
       const int hi = lo + (d == 0 ? 1 : (d == 1 ? sbox3_i(1) : sbox3_i(2) * sbox3_j(2)));
 #pragma unroll
@@ -554,7 +560,7 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
 }
 
 template <typename T, int NS, bool VISC, int MODE>
-__global__ void __launch_bounds__(T3I * T3J * T3K, sizeof(T) == 4 ? 2 : 1) tile3d_kernel(StageParams<T> P) {
+__global__ void __launch_bounds__(T3I * T3J * tile3d_tk(sizeof(T) == 4), 1) tile3d_kernel(StageParams<T> P) {
   extern __shared__ __align__(16) unsigned char smraw[];
   tile3d<T, NS, VISC, MODE>(P, blockIdx.x, reinterpret_cast<T*>(smraw));
 }
