@@ -173,8 +173,11 @@ struct Two<double> {
   static __device__ __forceinline__ double2 ld(const double* p) { return *reinterpret_cast<const double2*>(p); }
 };
 
-// an int index descriptor carried in a slot of a floating-point record
-__device__ __forceinline__ float int_in(float, int v) { return __int_as_float(v); }
+// an int index descriptor (fields below bit 30) carried in a slot of a
+// floating-point record; in FP32 bit 30 is set so that the pattern is a
+// normal number (never a denormal that a flush-to-zero path could clear, nor a
+// NaN); the decoder masks its fields and ignores that bit
+__device__ __forceinline__ float int_in(float, int v) { return __int_as_float(v | 0x40000000); }
 __device__ __forceinline__ double int_in(double, int v) { return (double)v; }
 __device__ __forceinline__ int int_of(float x) { return __float_as_int(x); }
 __device__ __forceinline__ int int_of(double x) { return (int)x; }
@@ -602,7 +605,7 @@ __device__ __forceinline__ void tile2d(const StageParams<T>& P, int t, T* sm) {
   constexpr int FRW = tile2d_face_words(VISC);
   T* sFR = sAcc + (BALG ? 0 : NS * NV * NT);   // [NF][FRW] per face work item: (vg, dcx, dcy, descriptor), or (vg, descriptor) inviscid
   T* sD = sFR + FRW * NF;   // [NS][NS]
-  static_assert(RI * (TJ + 4) <= 512 && NF <= 1024 && GI * (TJ + 2) <= 512, "face descriptor fields");
+  static_assert(RI * (TJ + 4) <= 512 && NF <= 1024 && GI * (TJ + 2) <= 508, "face descriptor fields");
   static_assert(!BALG || (NS > 0 && NS <= kMaxStaticNS), "global balances: static N_s");
   T* const bal = (BALG && MODE == 1) ? P.R + (int64_t)t * kMaxStaticNS * NV * NT : nullptr;
   if (BALG && P.R == nullptr) return;   // no scratch passed (the host refuses such a launch first)
