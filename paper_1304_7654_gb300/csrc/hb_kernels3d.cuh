@@ -306,7 +306,8 @@ __device__ __forceinline__ void tile3d(const StageParams<T>& P, int t, T* sm) {
       // per quantity into the frame of snapshot n (the sum is linear in S)
       // only the ring cells that are L or R of a tile face: the tile and its
       // six face-adjacent slabs (the ring's edges and corners are never read),
-      // NGU = 512 work items, two full rounds of the 256 threads
+      // NGU work items (896 for an 8x8x8 tile on 512 threads, 512 for an 8x8x4
+      // tile on 256: two full rounds)
       for (int w = tid; w < NGU; w += nt) {
         int gi, gj, gk;
         if (w < NT) {
